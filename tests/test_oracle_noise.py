@@ -1,0 +1,105 @@
+"""Pins of the oracle's noise generator (CPU only).
+
+Philox4x32-10 is pinned to the published known-answer vectors of Salmon et al.
+(SC'11); the uniform map and Box-Muller (Sec. 4.1: two uniforms -> two
+Gaussians) to closed-form values and to the moments of the standard normal.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+
+
+def _kat(golden_dir):
+    rows = []
+    with open(os.path.join(golden_dir, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            vals = [int(t, 16) for t in line.split()]
+            rows.append((vals[0:4], vals[4:6], vals[6:10]))
+    return rows
+
+
+def test_philox_known_answers(golden_dir):
+    rows = _kat(golden_dir)
+    assert len(rows) == 3
+    for ctr, key, expect in rows:
+        got = oracle.philox4x32_10(ctr, key)[0]
+        assert [int(x) for x in got] == expect
+
+
+def test_philox_counter_sensitivity():
+    # Changing any one counter or key bit changes all four output words.
+    base = oracle.philox4x32_10([1, 2, 3, 4], [5, 6])[0]
+    for pos in range(4):
+        ctr = [1, 2, 3, 4]
+        ctr[pos] ^= 1
+        out = oracle.philox4x32_10(ctr, [5, 6])[0]
+        assert np.all(out != base)
+
+
+def test_uniform_range_and_exactness():
+    # u = ((w >> 8) + 1) * 2^-24 lies in (0, 1] and is exact in float32.
+    assert oracle.uniform(0) == 2.0 ** -24
+    assert oracle.uniform(0xFFFFFFFF) == 1.0
+    assert oracle.uniform(0x800000FF) == 0.5 + 2.0 ** -24
+    rng = np.random.default_rng(3)
+    for w in rng.integers(0, 2 ** 32, size=2000, dtype=np.uint64):
+        u = oracle.uniform(int(w))
+        assert 0.0 < u <= 1.0
+        assert float(np.float32(u)) == u
+
+
+def test_box_muller_closed_form():
+    # u0 = 1/2, u1 = 1/4: rho = sqrt(2 ln 2), angle pi/2 -> (0, rho).
+    w_half = ((1 << 23) - 1) << 8
+    w_quarter = ((1 << 22) - 1) << 8
+    assert oracle.uniform(w_half) == 0.5 and oracle.uniform(w_quarter) == 0.25
+    z0, z1 = oracle.box_muller(w_half, w_quarter)
+    rho = math.sqrt(2.0 * math.log(2.0))
+    assert abs(z0) < 1e-15 and abs(z1 - rho) < 1e-15
+    # u0 = 1: log(1) = 0 -> both zero.
+    z0, z1 = oracle.box_muller(0xFFFFFFFF, 12345)
+    assert z0 == 0.0 and z1 == 0.0
+    # Largest radius: u0 = 2^-24 -> rho = sqrt(48 ln 2).
+    z0, z1 = oracle.box_muller(0, 0)
+    assert abs(math.hypot(z0, z1) - math.sqrt(48.0 * math.log(2.0))) < 1e-13
+
+
+def test_gaussian_stream_layout():
+    # Steps 4g..4g+3 of one stream take (z0, z1) from words (0, 1) and (z2, z3)
+    # from words (2, 3) of the Philox block with counter (g, c1, c2, tag).
+    seed, tag, c1, c2 = 0x1234_5678_9ABC, 1, 77, 5
+    key = oracle.seed_key(seed)
+    for g in (0, 1, 1000):
+        w = oracle.philox4x32_10([g, c1, c2, tag], key)[0]
+        a = oracle.box_muller(w[0], w[1])
+        b = oracle.box_muller(w[2], w[3])
+        got = [oracle.gaussian(seed, tag, c1, c2, 4 * g + k) for k in range(4)]
+        assert got == [a[0], a[1], b[0], b[1]]
+
+
+def test_gaussian_moments():
+    n = 200_000
+    z = np.array([oracle.gaussian(7, 1, i % 1000, i // 1000, 3) for i in range(n)])
+    se = 1.0 / math.sqrt(n)
+    assert abs(z.mean()) < 4 * se
+    assert abs(z.var() - 1.0) < 4 * math.sqrt(2.0) * se
+    assert abs(stats.skew(z)) < 4 * math.sqrt(6.0) * se
+    assert abs(stats.kurtosis(z, fisher=False) - 3.0) < 4 * math.sqrt(24.0) * se
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+
+
+def test_streams_uncorrelated():
+    n = 50_000
+    a = np.array([oracle.gaussian(0, 1, i, 0, 11) for i in range(n)])
+    b = np.array([oracle.gaussian(0, 1, i, 1, 11) for i in range(n)])
+    c = np.array([oracle.gaussian(0, 1, i, 0, 12) for i in range(n)])
+    for u, w in ((a, b), (a, c)):
+        assert abs(np.corrcoef(u, w)[0, 1]) < 4.0 / math.sqrt(n)
