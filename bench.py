@@ -1,0 +1,373 @@
+"""Benchmark of the ensemble-SDE hot path on GB300.
+
+Default workload: the batched Josephson sweep (Eq. 1 over 512 parameter points,
+uneven path and step counts, one persistent graph-captured launch, FP64
+on-device reductions).  One step = one full sweep from the initial state:
+Philox4x32-10 + Box-Muller noise, SRK2 (Alg. 2) for every path of every point,
+window averages and the FP64 ensemble reduction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sweep|plain|kuramoto-meanfield|kuramoto-pairwise]
+
+Prints one JSON line (rank 0).  Under torchrun each rank integrates its own copy
+of the workload (a different noise seed), with no data-path collective: weak
+scaling.  `--impl reference` times the FP64 CPU oracle on a bounded sample of
+the same workload on this host's cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0903_3852_gb300 import inputs  # noqa: E402
+
+PAPER_FLOP_PER_STEP = 79  # Table 1 (Appendix): FLOP per SRK2 step of Eq. 1, weighted
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pairwise-steps", type=int, default=200,
+                    help="steps per bench step of the pairwise Kuramoto workload")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workloads
+def sweep_workload(rank):
+    w = inputs.josephson_sweep()
+    # each rank integrates its own copy with its own noise key (weak scaling)
+    w["seed"] = w["seed"] + 1000 * rank
+    return w
+
+
+def plain_workload(rank):
+    w = inputs.josephson_plain()
+    w["seed"] = w["seed"] + 1000 * rank
+    return w
+
+
+def fp32_peak_tflops(props):
+    # 128 FP32 lanes per SM on Blackwell, one FMA (2 FLOP) per lane per clock,
+    # at the maximum SM clock of 2070 MHz.
+    return props.multi_processor_count * 128 * 2 * 2.070e9 / 1e12
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    from paper_0903_3852_gb300 import build as sde_build
+    from paper_0903_3852_gb300 import sde
+
+    sde_build.build()
+    props = torch.cuda.get_device_properties(device)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    if args.workload in ("sweep", "plain"):
+        w = sweep_workload(rank) if args.workload == "sweep" else plain_workload(rank)
+        sched = sde.SDE_SCHED_PERSISTENT if args.workload == "sweep" else sde.SDE_SCHED_PLAIN
+        ens = sde.Ensemble.josephson(w["points"], w["paths"], w["steps"], w["seed"],
+                                     steps_per_period=w["steps_per_period"], schedule=sched)
+        n = int(w["paths"].sum())
+        units = float((w["paths"] * w["steps"]).sum())
+        n_end = int(w["steps"].max())
+        x_h = torch.from_numpy(w["x0"]).pin_memory()
+        v_h = torch.from_numpy(w["v0"]).pin_memory()
+        x_in, v_in = x_h.to(device), v_h.to(device)
+        x_out = torch.empty_like(x_in)
+        v_out = torch.empty_like(v_in)
+        w_out = torch.empty(n, dtype=torch.int32, device=device)
+        vs_out = torch.empty(n, dtype=torch.float64, device=device)
+
+        def step():
+            ens.run_josephson(0, n_end, x_in, v_in, x_out, v_out, w_out, vs_out)
+
+        def step_e2e():
+            x_in.copy_(x_h, non_blocking=True)
+            v_in.copy_(v_h, non_blocking=True)
+            step()
+            return ens.observables()
+
+        h2d = x_h.numel() * 4 + v_h.numel() * 4
+        d2h = 40 * len(w["points"])
+        launches_per_step = (1 if sched == sde.SDE_SCHED_PERSISTENT else len(w["points"])) + 1
+        metric = "path-steps/sec"
+        flop_per_unit = PAPER_FLOP_PER_STEP
+        cfg = {"workload": "josephson_sweep_512pts" if args.workload == "sweep" else "josephson_plain_1024",
+               "points": len(w["points"]), "total_paths": n, "path_steps": units,
+               "steps_per_period": w["steps_per_period"],
+               "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
+               "tuning": dict(zip(("block_threads", "paths_per_thread"), ens.tuning())),
+               "l2": "flushed between steps (256 MiB write); state 9 MB, compute-bound"}
+    else:
+        w = inputs.kuramoto_uniform(seed=rank)
+        model = sde.SDE_KURAMOTO_MEANFIELD if args.workload == "kuramoto-meanfield" else sde.SDE_KURAMOTO_PAIRWISE
+        S = w["steps"] if model == sde.SDE_KURAMOTO_MEANFIELD else args.pairwise_steps
+        ens = sde.Ensemble.kuramoto(model, w["n_osc"], w["replicas"], w["K"], w["D"], w["dt"], w["seed"],
+                                    sample_every=w["sample_every"])
+        phi_h = torch.from_numpy(w["phi0"]).pin_memory()
+        phi_in = phi_h.to(device)
+        om = torch.from_numpy(w["omega"]).to(device)
+        phi_out = torch.empty_like(phi_in)
+
+        def step():
+            ens.run_kuramoto(0, S, phi_in, phi_out, om)
+
+        def step_e2e():
+            phi_in.copy_(phi_h, non_blocking=True)
+            step()
+            return ens.observables()
+
+        h2d = phi_h.numel() * 4
+        d2h = 40 * (S // w["sample_every"] + 1)
+        if model == sde.SDE_KURAMOTO_MEANFIELD:
+            units = float(w["n_osc"] * w["replicas"] * S)
+            metric = "oscillator-steps/sec"
+            flop_per_unit = 66  # Appendix: 66 FLOP per step of the mean-field program
+            launches_per_step = 4
+        else:
+            units = float(w["n_osc"] ** 2 * w["replicas"] * S)
+            metric = "pair-terms/sec"
+            flop_per_unit = 6  # Appendix: 44 + 6N FLOP per oscillator-step, 6 per pair term
+            launches_per_step = 2 * S + S // w["sample_every"] + 4
+        cfg = {"workload": "kuramoto_%s_N%d_R%d" % (args.workload.split("-")[1], w["n_osc"], w["replicas"]),
+               "steps_per_bench_step": S, "K": w["K"], "D": w["D"], "dt": w["dt"],
+               "l2": "flushed between steps (256 MiB write)"}
+
+    # warm-up (also captures the graph)
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device if isinstance(device, int) else torch.cuda.current_device())
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kernel_ms = []
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        kernel_ms.append(ens.last_kernel_ms())
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_e2e()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = statistics.median(e2e_ms)
+
+    k_ms = statistics.mean(kernel_ms)
+    achieved = flop_per_unit * units / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(props)
+    res = {
+        "metric": metric,
+        "value": units * world / (ms * 1e-3),
+        "unit": metric.split("/")[0] + "/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (FP64 reductions)",
+        "data": "synthetic (seeded; inputs.py)",
+        "config": cfg,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "flop_model": "%d FLOP per unit (paper Table 1 weighting)" % flop_per_unit,
+                     "peak_source": "%d SM x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)"
+                                    % props.multi_processor_count,
+                     "kernel_ms": k_ms},
+        "e2e": {"value": units * world / (e2e * 1e-3), "unit": metric.split("/")[0] + "/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    return res, ens
+
+
+def cpu_baseline(args, budget_s=20.0):
+    """The FP64 oracle as it stands, on a bounded sample of the workload."""
+    import oracle
+    if args.workload in ("sweep", "plain"):
+        w = sweep_workload(0) if args.workload == "sweep" else plain_workload(0)
+        offs = np.concatenate([[0], np.cumsum(w["paths"])])
+        per_point = 2 if args.workload == "sweep" else 64
+        t0 = time.perf_counter()
+        done = 0.0
+        npts = 0
+        for k, pt in enumerate(w["points"]):
+            sl = slice(offs[k], offs[k] + min(per_point, int(w["paths"][k])))
+            S = int(w["steps"][k])
+            oracle.jj_run(w["x0"][sl], w["v0"][sl], oracle.jj_params(**pt), w["steps_per_period"], 0, S, S,
+                          w["seed"], point=k)
+            done += (sl.stop - sl.start) * S
+            npts += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": done / dt, "unit": "path-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "first %d paths of each of %d points, full step counts (%.3g path-steps)"
+                          % (per_point, npts, done)}
+    w = inputs.kuramoto_uniform()
+    meanfield = args.workload == "kuramoto-meanfield"
+    S = 200 if meanfield else 2
+    t0 = time.perf_counter()
+    oracle.kuramoto_run(w["phi0"][0], w["omega"][0], w["D"], w["dt"], 0, S, w["seed"], 0,
+                        Kconst=w["K"] / w["n_osc"], meanfield=meanfield)
+    dt = time.perf_counter() - t0
+    units = w["n_osc"] * S if meanfield else w["n_osc"] ** 2 * S
+    unit = "oscillator-steps/s" if meanfield else "pair-terms/s"
+    return {"value": units / dt, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": "replica 0, %d steps" % S}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, K bounded steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return None
+    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(args, budget_s=min(per, 3.0))
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(args, budget_s=per)
+        vals.append(last["value"])
+    v = statistics.mean(vals)
+    metric = {"sweep": "path-steps/sec", "plain": "path-steps/sec",
+              "kuramoto-meanfield": "oscillator-steps/sec", "kuramoto-pairwise": "pair-terms/sec"}[args.workload]
+    unit = last["unit"]
+    res = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; inputs.py)",
+           "config": {"workload": args.workload, "sample": last["sample"]},
+           "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": last["sample"]},
+           "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        res = run_reference(args)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res, ens = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = cpu_baseline(args)
+        elif not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(res))
+    ens.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

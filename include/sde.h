@@ -1,0 +1,225 @@
+/*
+ * sde.h -- C ABI of the GB300 ensemble-SDE library (libsde_gb300.so).
+ *
+ * Januszewski & Kostur, "Accelerating numerical solution of stochastic
+ * differential equations with CUDA" (arXiv:0903.3852).  The library
+ * integrates many independent realisations of
+ *   Eq. 1 (Sec. 3)  x'' + gamma x' = -2 pi cos(2 pi x) + a cos(omega t) + f
+ *                                   + sqrt(2 gamma D) xi(t)
+ *   Eq. 2 (Sec. 3)  x_i' = omega_i + sum_j K_ij sin(x_j - x_i) + sqrt(2 D) xi_i(t)
+ *                   (gamma = 1)
+ * with the second-order stochastic Runge-Kutta step of Alg. 2 (Heun form,
+ * the same Gaussian in both stages), Gaussian noise from Philox4x32-10
+ * counters through Box-Muller (Sec. 4.1), and FP64 on-device ensemble
+ * reductions (Sec. 4.1, ensemble averages; Sec. 5, <<v>>).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees them.  *_host pointers are ordinary host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every kernel goes on that stream; no entry point
+ *    synchronises the device except sde_observables and sde_last_kernel_ms.
+ *  - Every entry point returns an sde_status; on failure the thread-local
+ *    message from sde_last_error() says why.  No exception crosses the ABI.
+ *  - Asynchronous device faults found by the kernels (non-finite state, a
+ *    bounded wait that expired) are latched in the context and returned by
+ *    the next sde_observables call.
+ */
+#ifndef SDE_GB300_H_
+#define SDE_GB300_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sde_status {
+  SDE_OK = 0,
+  SDE_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+  SDE_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has it)   */
+  SDE_ERR_NO_MEMORY = 3,   /* device or host allocation failed             */
+  SDE_ERR_TIMEOUT = 4,     /* a bounded device wait expired                */
+  SDE_ERR_UNSUPPORTED = 5, /* valid request this build does not implement  */
+  SDE_ERR_NUMERIC = 6      /* a kernel produced a non-finite state         */
+} sde_status;
+
+typedef enum sde_model {
+  SDE_JOSEPHSON = 0,          /* Eq. 1, per-path kernels (Alg. 1)              */
+  SDE_KURAMOTO_MEANFIELD = 1, /* Eq. 2, K_ij = K/N, mean-field sums (Eq. 3)     */
+  SDE_KURAMOTO_PAIRWISE = 2,  /* Eq. 2, K_ij = K/N, direct all-pairs sum (Alg. 3) */
+  SDE_KURAMOTO_GENERAL = 3,   /* Eq. 2, matrix K_ij: BF16 tensor-core GEMM      */
+  SDE_KURAMOTO_GENERAL_FP32 = 4 /* Eq. 2, matrix K_ij: FP32 CUDA-core baseline  */
+} sde_model;
+
+/* Josephson launch schedules. */
+typedef enum sde_schedule {
+  SDE_SCHED_PERSISTENT = 0, /* all points in one persistent launch with a work
+                               queue ordered longest-first, graph-captured   */
+  SDE_SCHED_PLAIN = 1       /* one launch per point, one thread per path
+                               (the per-path kernel of Alg. 1)               */
+} sde_schedule;
+
+/* Flags for sde_config.flags. */
+#define SDE_FLAG_NO_GRAPH 1u /* launch kernels directly instead of replaying a graph */
+
+/* One parameter point of Eq. 1. */
+typedef struct sde_jj_point {
+  double gamma; /* friction, > 0                          */
+  double a;     /* drive amplitude                        */
+  double omega; /* drive angular frequency, > 0           */
+  double f;     /* constant bias                          */
+  double D;     /* noise intensity k_B T, >= 0            */
+} sde_jj_point;
+
+typedef struct sde_config {
+  int32_t model;    /* sde_model                                             */
+  int32_t schedule; /* sde_schedule (Josephson only)                         */
+  uint64_t seed;    /* Philox key: (seed & 0xffffffff, seed >> 32)           */
+
+  /* ---- Josephson (Eq. 1) -------------------------------------------- */
+  int32_t n_points;         /* >= 1                                          */
+  int32_t steps_per_period; /* P in [1, 4096]: dt_k = 2 pi / (omega_k P); the
+                               drive phase is kept as the integer n mod P
+                               (time modulo the period, Sec. 5)             */
+  const sde_jj_point *points; /* host, n_points entries; copied at create  */
+  const int64_t *paths;       /* host, paths per point, each in [0, 2^31)   */
+  const int64_t *steps;       /* host, total steps S_k per point, [0, 2^33];
+                                 <v> averages v over the last floor(S_k/2)
+                                 states                                     */
+
+  /* ---- Kuramoto (Eq. 2) --------------------------------------------- */
+  int64_t n_osc;        /* N oscillators per replica                        */
+  int64_t n_replicas;   /* independent replicas                             */
+  double K;             /* uniform models: K_ij = K / N                     */
+  double D;             /* noise intensity                                  */
+  double dt;            /* time step                                        */
+  int32_t sample_every; /* M: r(t) is sampled every M steps (M = 100 in the
+                           paper, Sec. 4.1); 0 = no samples                  */
+
+  /* ---- tuning --------------------------------------------------------- */
+  int32_t block_threads;    /* threads per block; 0 = autotune               */
+  int32_t paths_per_thread; /* Josephson paths per thread (1 or 2); 0 = autotune */
+  uint32_t flags;           /* SDE_FLAG_*                                     */
+} sde_config;
+
+/*
+ * Arguments of one sde_run_ensemble call.  The state arrays are
+ * caller-owned device buffers; *_in and *_out may alias (in-place run).
+ *
+ * Josephson layout: structure of arrays, point-major: the paths of point 0,
+ * then those of point 1, ... (total = sum of paths).  Position is stored as
+ * a fractional part x in [0, 1) plus an int32 winding count w (x_abs = w +
+ * x); the kernels wrap any x_in on load.  vsum holds the running sum of v
+ * over the averaging window (FP64).  w_in and vsum_in may be NULL (zeros).
+ *
+ * Kuramoto layout: replica-major [replica][oscillator], phases in radians;
+ * phi_out is wrapped to [0, 2 pi).  omega is [replica][oscillator].
+ */
+typedef struct sde_run_desc {
+  int64_t n_begin; /* first step index (the noise counter)                  */
+  int64_t n_end;   /* one past the last step; Josephson points stop at S_k  */
+  /* Josephson */
+  const float *x_in_dev;
+  const float *v_in_dev;
+  const int32_t *w_in_dev;
+  const double *vsum_in_dev;
+  float *x_out_dev;
+  float *v_out_dev;
+  int32_t *w_out_dev;
+  double *vsum_out_dev;
+  /* Kuramoto */
+  const float *phi_in_dev;
+  float *phi_out_dev;
+  const float *omega_dev;
+  double *r_out_dev; /* [n_samples][n_replicas] or NULL; n_samples =
+                        ceil((n_end - n_begin) / M) + 1, the last at n_end  */
+} sde_run_desc;
+
+/* One row of observables (FP64). */
+typedef struct sde_obs_row {
+  double mean;  /* Josephson: ensemble mean of the per-path time average of v
+                   over the window; Kuramoto: mean over replicas of r(t)     */
+  double var;   /* unbiased variance of the same per-path / per-replica values */
+  double se;    /* standard error sqrt(var / count)                         */
+  double count; /* number of paths (replicas) in the row                    */
+  double t;     /* Josephson: time at the end of the window; Kuramoto: t_n  */
+} sde_obs_row;
+
+typedef struct sde_ctx sde_ctx; /* opaque, library-owned */
+
+/*
+ * Validate cfg, copy the parameter tables to the device, allocate the
+ * library workspace (work list, reduction partials, observables) and, if
+ * block_threads or paths_per_thread is 0, autotune the launch shape by
+ * timing short runs of each candidate on the current device.  The context
+ * is bound to the current CUDA device.
+ * Errors: SDE_ERR_INVALID_ARG (bad sizes or parameters), SDE_ERR_NO_MEMORY,
+ * SDE_ERR_CUDA.  On error *out is NULL.
+ */
+sde_status sde_create(const sde_config *cfg, sde_ctx **out);
+
+/*
+ * Advance the ensemble from step run->n_begin to run->n_end on `stream`
+ * (Alg. 1: load state, loop over steps, store state) and reduce the
+ * observables on the device (FP64).  Josephson points whose S_k <= n_begin
+ * are left unchanged.  Asynchronous; the state buffers must stay valid
+ * until the stream reaches the end of the call's work.
+ * Errors: SDE_ERR_INVALID_ARG (NULL required pointer, n_end < n_begin),
+ * SDE_ERR_CUDA (launch failure).
+ */
+sde_status sde_run_ensemble(sde_ctx *ctx, const sde_run_desc *run, void *stream);
+
+/*
+ * Synchronise the stream of the last run and copy the observables of that
+ * run to rows_host: one row per point (Josephson) or per sample time
+ * (Kuramoto).  *n_rows receives the row count; if capacity is smaller, only
+ * the first `capacity` rows are copied.  Returns the latched device status
+ * (SDE_ERR_NUMERIC, SDE_ERR_TIMEOUT) if a kernel reported one.
+ */
+sde_status sde_observables(sde_ctx *ctx, sde_obs_row *rows_host, int64_t capacity,
+                           int64_t *n_rows);
+
+/* Free the context and its workspace.  NULL-safe.  Synchronises the device. */
+void sde_destroy(sde_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *sde_last_error(void);
+
+/* Launch shape chosen at create (after autotuning). */
+sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads,
+                          int32_t *paths_per_thread);
+
+/*
+ * Device time in milliseconds of the dominant kernel of the last run
+ * (CUDA events recorded on the run's stream around that kernel).
+ * Synchronises that stream.
+ */
+sde_status sde_last_kernel_ms(sde_ctx *ctx, float *ms);
+
+/*
+ * Philox4x32-10 (Salmon et al., SC'11; replaces the xorshift generator of
+ * Sec. 4.1): out_dev[4i..4i+3] = Philox(counter ctr_dev[4i..4i+3], key =
+ * (seed low word, seed high word)).  n counters, n >= 0, device arrays.
+ */
+sde_status sde_philox4x32_10(const uint32_t *ctr_dev, uint64_t seed, uint32_t *out_dev,
+                             int64_t n, void *stream);
+
+/*
+ * Box-Muller Gaussians (Sec. 4.1) as the integrators draw them: for each of
+ * the n counters, z_dev[4i..4i+3] = (z0, z1) from words (0, 1) and (z2, z3)
+ * from words (2, 3), with u = ((w >> 8) + 1) 2^-24, z0 = sqrt(-2 ln u0)
+ * cos(2 pi u1), z1 = sqrt(-2 ln u0) sin(2 pi u1), in FP32.
+ */
+sde_status sde_box_muller(const uint32_t *ctr_dev, uint64_t seed, float *z_dev, int64_t n,
+                          void *stream);
+
+/* Version of this ABI (major * 100 + minor). */
+int32_t sde_abi_version(void);
+
+#ifdef __cplusplus
+} /* extern "C" */
+#endif
+
+#endif /* SDE_GB300_H_ */

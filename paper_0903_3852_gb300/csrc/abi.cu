@@ -1,0 +1,538 @@
+// abi.cu -- the C ABI of include/sde.h: context creation, validation,
+// autotuning, graph capture and the observables round trip.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kuramoto.h"
+
+namespace sde {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+sde_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorName(e) + " (" +
+            cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? SDE_ERR_NO_MEMORY : SDE_ERR_CUDA;
+}
+
+}  // namespace sde
+
+using namespace sde;
+
+struct sde_ctx {
+  sde_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  // ---- Josephson ----
+  int n_points = 0;
+  int P = 0;
+  int64_t total_paths = 0;
+  std::vector<int64_t> paths, steps, offsets;
+  JJConsts *consts = nullptr;
+  float *drive = nullptr;
+  JJUnitList units[3];  // indexed by ILP (1, 2)
+  Moments *partials = nullptr;
+  uint32_t *queue = nullptr;
+  int block = 0, ilp = 0;
+  // ---- Kuramoto ----
+  KuramotoCtx *kur = nullptr;
+  // ---- common ----
+  sde_obs_row *obs = nullptr;
+  int64_t n_obs_rows = 0;
+  int64_t max_obs_rows = 0;
+  uint32_t *err = nullptr;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  // graph cache
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  sde_run_desc gdesc{};
+  bool gvalid = false;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+void free_ctx(sde_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  cudaFree(c->consts);
+  cudaFree(c->drive);
+  for (auto &u : c->units) {
+    cudaFree(u.units);
+    cudaFree(u.point_range);
+  }
+  cudaFree(c->partials);
+  cudaFree(c->queue);
+  cudaFree(c->obs);
+  cudaFree(c->err);
+  kuramoto_destroy(c->kur);
+  delete c;
+}
+
+// Work list: units of 32 * ilp paths, ordered by decreasing step count
+// (longest-processing-time-first), ties by point index, so that the units of
+// one point stay contiguous.
+sde_status build_units(sde_ctx *c, int ilp) {
+  JJUnitList &L = c->units[ilp];
+  L.ilp = ilp;
+  const int per = 32 * ilp;
+  std::vector<int> order(c->n_points);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return c->steps[a] > c->steps[b]; });
+  std::vector<JJUnit> units;
+  L.point_range_h.assign(c->n_points, make_int2(0, 0));
+  for (int p : order) {
+    const int first = (int)units.size();
+    for (int64_t b = 0; b < c->paths[p]; b += per) {
+      JJUnit u;
+      u.point = p;
+      u.path_begin = (int32_t)b;
+      u.n_paths = (int32_t)std::min<int64_t>(per, c->paths[p] - b);
+      u.pad = 0;
+      units.push_back(u);
+    }
+    L.point_range_h[p] = make_int2(first, (int)units.size());
+  }
+  L.n_units = (int32_t)units.size();
+  SDE_CUDA_TRY(dmalloc(&L.units, units.size()));
+  SDE_CUDA_TRY(dmalloc(&L.point_range, c->n_points));
+  if (!units.empty())
+    SDE_CUDA_TRY(cudaMemcpy(L.units, units.data(), sizeof(JJUnit) * units.size(),
+                            cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(L.point_range, L.point_range_h.data(), sizeof(int2) * c->n_points,
+                          cudaMemcpyHostToDevice));
+  return SDE_OK;
+}
+
+JJLaunchArgs jj_args(const sde_ctx *c, const sde_run_desc *r, int ilp) {
+  JJLaunchArgs a{};
+  a.consts = c->consts;
+  a.units = c->units[ilp].units;
+  a.drive = c->drive;
+  a.P = c->P;
+  a.unit_begin = 0;
+  a.unit_end = c->units[ilp].n_units;
+  a.queue = nullptr;
+  a.partials = c->partials;
+  a.err = c->err;
+  a.st = JJState{r->x_in_dev, r->v_in_dev, r->w_in_dev, r->vsum_in_dev,
+                 r->x_out_dev, r->v_out_dev, r->w_out_dev, r->vsum_out_dev};
+  a.n_begin = r->n_begin;
+  a.n_end = r->n_end;
+  a.seed = c->cfg.seed;
+  return a;
+}
+
+int persistent_grid(const sde_ctx *c, int ilp, int block) {
+  const int per_sm = jj_max_blocks_per_sm(ilp, block, c->P);
+  const int warps = block / 32;
+  const int need = (c->units[ilp].n_units + warps - 1) / warps;
+  int grid = std::max(1, per_sm) * c->sm_count;
+  return std::max(1, std::min(grid, need));
+}
+
+// Enqueue the work of one Josephson run (no graph).
+sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp, int block,
+                      bool time_it) {
+  JJLaunchArgs a = jj_args(c, r, ilp);
+  const JJUnitList &L = c->units[ilp];
+  if (time_it) SDE_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  if (c->cfg.schedule == SDE_SCHED_PERSISTENT) {
+    if (L.n_units > 0) {
+      SDE_CUDA_TRY(cudaMemsetAsync(c->queue, 0, sizeof(uint32_t), s));
+      a.queue = c->queue;
+      SDE_CUDA_TRY(jj_launch(a, ilp, block, persistent_grid(c, ilp, block), s));
+    }
+  } else {
+    const int warps = block / 32;
+    for (int p = 0; p < c->n_points; ++p) {
+      const int2 pr = L.point_range_h[p];
+      if (pr.y <= pr.x) continue;
+      a.unit_begin = pr.x;
+      a.unit_end = pr.y;
+      const int grid = (pr.y - pr.x + warps - 1) / warps;
+      SDE_CUDA_TRY(jj_launch(a, ilp, block, grid, s));
+    }
+  }
+  if (time_it) SDE_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  SDE_CUDA_TRY(jj_finalize(c->consts, L.point_range, c->n_points, c->partials, r->n_end, c->obs, s));
+  return SDE_OK;
+}
+
+// Time each candidate launch shape on a short run over every point and keep
+// the fastest.  Uses scratch state, so the caller's buffers are untouched.
+sde_status jj_autotune(sde_ctx *c) {
+  std::vector<std::pair<int, int>> cand;
+  const bool fixed_block = c->cfg.block_threads > 0;
+  const bool fixed_ilp = c->cfg.paths_per_thread > 0;
+  const int blocks[] = {128, 256, 512};
+  const int plain_blocks[] = {64, 128, 256, 512};
+  std::vector<int> bl;
+  if (fixed_block)
+    bl.push_back(c->cfg.block_threads);
+  else if (c->cfg.schedule == SDE_SCHED_PLAIN)
+    bl.assign(std::begin(plain_blocks), std::end(plain_blocks));
+  else
+    bl.assign(std::begin(blocks), std::end(blocks));
+  std::vector<int> il;
+  if (fixed_ilp)
+    il.push_back(c->cfg.paths_per_thread);
+  else if (c->cfg.schedule == SDE_SCHED_PLAIN)
+    il.push_back(1);  // the per-path kernel of Alg. 1: one thread per path
+  else
+    il = {1, 2};
+  for (int b : bl)
+    for (int i : il) cand.push_back({b, i});
+  if (cand.size() == 1) {
+    c->block = cand[0].first;
+    c->ilp = cand[0].second;
+    return SDE_OK;
+  }
+  const int64_t np = std::max<int64_t>(c->total_paths, 1);
+  float *x = nullptr, *v = nullptr;
+  int32_t *w = nullptr;
+  double *vs = nullptr;
+  sde_status st = SDE_OK;
+  cudaStream_t s = nullptr;
+  auto fail = [&](cudaError_t e, const char *what) {
+    st = cuda_fail(e, what);
+  };
+  cudaError_t e;
+  if ((e = dmalloc(&x, np)) != cudaSuccess) fail(e, "autotune alloc");
+  if (st == SDE_OK && (e = dmalloc(&v, np)) != cudaSuccess) fail(e, "autotune alloc");
+  if (st == SDE_OK && (e = dmalloc(&w, np)) != cudaSuccess) fail(e, "autotune alloc");
+  if (st == SDE_OK && (e = dmalloc(&vs, np)) != cudaSuccess) fail(e, "autotune alloc");
+  if (st == SDE_OK && (e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+    fail(e, "autotune stream");
+  if (st == SDE_OK) {
+    cudaMemsetAsync(x, 0, sizeof(float) * np, s);
+    cudaMemsetAsync(v, 0, sizeof(float) * np, s);
+    sde_run_desc r{};
+    r.n_begin = 0;
+    int64_t max_steps = 0;
+    for (auto S : c->steps) max_steps = std::max(max_steps, S);
+    r.n_end = std::min<int64_t>(max_steps, 768);
+    r.x_in_dev = x;
+    r.v_in_dev = v;
+    r.x_out_dev = x;
+    r.v_out_dev = v;
+    r.w_out_dev = w;
+    r.vsum_out_dev = vs;
+    float best = 1e30f;
+    for (auto &cd : cand) {
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 3 && st == SDE_OK; ++rep) {
+        st = jj_enqueue(c, &r, s, cd.second, cd.first, true);
+        if (st != SDE_OK) break;
+        if ((e = cudaEventSynchronize(c->ev1)) != cudaSuccess) {
+          fail(e, "autotune sync");
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        if (rep > 0) ms_min = std::min(ms_min, ms);
+      }
+      if (st != SDE_OK) break;
+      if (ms_min < best) {
+        best = ms_min;
+        c->block = cd.first;
+        c->ilp = cd.second;
+      }
+    }
+    if (st == SDE_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) fail(e, "autotune sync");
+    if (st == SDE_OK) cudaMemset(c->err, 0, sizeof(uint32_t));
+  }
+  if (s) cudaStreamDestroy(s);
+  cudaFree(x);
+  cudaFree(v);
+  cudaFree(w);
+  cudaFree(vs);
+  return st;
+}
+
+sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
+  SDE_CHECK_ARG(cfg->n_points >= 1, "n_points must be >= 1");
+  SDE_CHECK_ARG(cfg->points && cfg->paths && cfg->steps, "points/paths/steps must be non-NULL");
+  SDE_CHECK_ARG(cfg->steps_per_period >= 1 && cfg->steps_per_period <= 4096,
+                "steps_per_period must be in [1, 4096]");
+  SDE_CHECK_ARG(cfg->schedule == SDE_SCHED_PERSISTENT || cfg->schedule == SDE_SCHED_PLAIN,
+                "unknown schedule");
+  SDE_CHECK_ARG(cfg->block_threads == 0 ||
+                    (cfg->block_threads >= 32 && cfg->block_threads <= 512 &&
+                     cfg->block_threads % 32 == 0),
+                "block_threads must be 0 or a multiple of 32 in [32, 512]");
+  SDE_CHECK_ARG(cfg->paths_per_thread >= 0 && cfg->paths_per_thread <= 2,
+                "paths_per_thread must be 0, 1 or 2");
+  c->n_points = cfg->n_points;
+  c->P = cfg->steps_per_period;
+  c->paths.resize(c->n_points);
+  c->steps.resize(c->n_points);
+  c->offsets.resize(c->n_points);
+  int64_t off = 0;
+  for (int p = 0; p < c->n_points; ++p) {
+    const sde_jj_point &q = cfg->points[p];
+    SDE_CHECK_ARG(isfinite(q.gamma) && isfinite(q.a) && isfinite(q.omega) && isfinite(q.f) &&
+                      isfinite(q.D),
+                  "point parameters must be finite");
+    SDE_CHECK_ARG(q.omega > 0.0, "omega must be > 0");
+    SDE_CHECK_ARG(q.gamma > 0.0, "gamma must be > 0");
+    SDE_CHECK_ARG(q.D >= 0.0, "D must be >= 0");
+    SDE_CHECK_ARG(cfg->paths[p] >= 0 && cfg->paths[p] < (1ll << 31), "paths out of range");
+    SDE_CHECK_ARG(cfg->steps[p] >= 0 && cfg->steps[p] <= (1ll << 33), "steps out of range");
+    c->paths[p] = cfg->paths[p];
+    c->steps[p] = cfg->steps[p];
+    c->offsets[p] = off;
+    off += cfg->paths[p];
+  }
+  c->total_paths = off;
+  SDE_CHECK_ARG(off < (1ll << 40), "total paths too large");
+
+  sde_jj_point *pts = nullptr;
+  int64_t *steps = nullptr, *offs = nullptr, *paths = nullptr;
+  SDE_CUDA_TRY(dmalloc(&pts, c->n_points));
+  SDE_CUDA_TRY(dmalloc(&steps, c->n_points));
+  SDE_CUDA_TRY(dmalloc(&offs, c->n_points));
+  SDE_CUDA_TRY(dmalloc(&paths, c->n_points));
+  SDE_CUDA_TRY(dmalloc(&c->consts, c->n_points));
+  SDE_CUDA_TRY(dmalloc(&c->drive, c->P));
+  SDE_CUDA_TRY(cudaMemcpy(pts, cfg->points, sizeof(sde_jj_point) * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(steps, c->steps.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(offs, c->offsets.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(paths, c->paths.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(jj_prepare(pts, c->n_points, c->P, steps, offs, paths, c->consts, c->drive, 0));
+  SDE_CUDA_TRY(cudaDeviceSynchronize());
+  cudaFree(pts);
+  cudaFree(steps);
+  cudaFree(offs);
+  cudaFree(paths);
+
+  int32_t max_units = 0;
+  for (int ilp = 1; ilp <= 2; ++ilp) {
+    sde_status st = build_units(c, ilp);
+    if (st != SDE_OK) return st;
+    max_units = std::max(max_units, c->units[ilp].n_units);
+  }
+  SDE_CUDA_TRY(dmalloc(&c->partials, max_units));
+  SDE_CUDA_TRY(dmalloc(&c->queue, 1));
+  c->max_obs_rows = c->n_points;
+  SDE_CUDA_TRY(dmalloc(&c->obs, c->max_obs_rows));
+  SDE_CUDA_TRY(cudaMemset(c->obs, 0, sizeof(sde_obs_row) * c->max_obs_rows));
+  return jj_autotune(c);
+}
+
+sde_status run_graph(sde_ctx *c, const sde_run_desc *r, cudaStream_t s) {
+  const bool same = c->gvalid && memcmp(&c->gdesc, r, sizeof(sde_run_desc)) == 0;
+  if (!same) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    c->gvalid = false;
+    cudaGraph_t g = nullptr;
+    SDE_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    sde_status st = jj_enqueue(c, r, c->cap_stream, c->ilp, c->block, true);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != SDE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    c->gdesc = *r;
+    c->gvalid = true;
+  }
+  SDE_CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+  return SDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sde_abi_version(void) { return 100; }
+
+const char *sde_last_error(void) { return g_last_error.c_str(); }
+
+sde_status sde_create(const sde_config *cfg, sde_ctx **out) {
+  clear_error();
+  if (!out) {
+    set_error("invalid argument: out is NULL");
+    return SDE_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  SDE_CHECK_ARG(cfg != nullptr, "cfg is NULL");
+  sde_ctx *c = new (std::nothrow) sde_ctx();
+  if (!c) {
+    set_error("host allocation failed");
+    return SDE_ERR_NO_MEMORY;
+  }
+  c->cfg = *cfg;
+  c->cfg.points = nullptr;
+  c->cfg.paths = nullptr;
+  c->cfg.steps = nullptr;
+  sde_status st = SDE_OK;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
+  if (st == SDE_OK &&
+      (e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess)
+    st = cuda_fail(e, "cudaDeviceGetAttribute");
+  if (st == SDE_OK && (e = dmalloc(&c->err, 1)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
+  if (st == SDE_OK && (e = cudaMemset(c->err, 0, sizeof(uint32_t))) != cudaSuccess)
+    st = cuda_fail(e, "cudaMemset");
+  if (st == SDE_OK && (e = cudaEventCreate(&c->ev0)) != cudaSuccess) st = cuda_fail(e, "cudaEventCreate");
+  if (st == SDE_OK && (e = cudaEventCreate(&c->ev1)) != cudaSuccess) st = cuda_fail(e, "cudaEventCreate");
+  if (st == SDE_OK && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    st = cuda_fail(e, "cudaStreamCreate");
+  if (st == SDE_OK) {
+    switch (cfg->model) {
+      case SDE_JOSEPHSON:
+        st = create_josephson(c, cfg);
+        break;
+      case SDE_KURAMOTO_MEANFIELD:
+      case SDE_KURAMOTO_PAIRWISE:
+      case SDE_KURAMOTO_GENERAL:
+      case SDE_KURAMOTO_GENERAL_FP32:
+        st = kuramoto_create(cfg, c->sm_count, c->err, &c->kur);
+        break;
+      default:
+        set_error("invalid argument: unknown model");
+        st = SDE_ERR_INVALID_ARG;
+    }
+  }
+  if (st != SDE_OK) {
+    std::string msg = g_last_error;
+    free_ctx(c);
+    set_error(msg);
+    return st;
+  }
+  *out = c;
+  return SDE_OK;
+}
+
+sde_status sde_run_ensemble(sde_ctx *c, const sde_run_desc *r, void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr && r != nullptr, "ctx and run must be non-NULL");
+  SDE_CHECK_ARG(r->n_begin >= 0 && r->n_end >= r->n_begin, "need 0 <= n_begin <= n_end");
+  SDE_CHECK_ARG(r->n_end <= (1ll << 33), "n_end out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = -1;
+  SDE_CUDA_TRY(cudaGetDevice(&dev));
+  SDE_CHECK_ARG(dev == c->device, "current device differs from the context's device");
+  if (c->cfg.model == SDE_JOSEPHSON) {
+    if (c->total_paths > 0) {
+      SDE_CHECK_ARG(r->x_in_dev && r->v_in_dev && r->x_out_dev && r->v_out_dev && r->w_out_dev &&
+                        r->vsum_out_dev,
+                    "Josephson run needs x_in, v_in, x_out, v_out, w_out and vsum_out");
+    }
+    sde_status st;
+    if (c->cfg.flags & SDE_FLAG_NO_GRAPH)
+      st = jj_enqueue(c, r, s, c->ilp, c->block, true);
+    else
+      st = run_graph(c, r, s);
+    if (st != SDE_OK) return st;
+    c->n_obs_rows = c->n_points;
+  } else {
+    int64_t rows = 0;
+    sde_status st = kuramoto_run(c->kur, r, s, c->ev0, c->ev1, c->obs, &c->obs, &c->max_obs_rows, &rows);
+    if (st != SDE_OK) return st;
+    c->n_obs_rows = rows;
+  }
+  c->last_stream = s;
+  c->timed = true;
+  return SDE_OK;
+}
+
+sde_status sde_observables(sde_ctx *c, sde_obs_row *rows, int64_t capacity, int64_t *n_rows) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
+  SDE_CHECK_ARG(capacity >= 0 && (rows != nullptr || capacity == 0), "rows/capacity");
+  SDE_CUDA_TRY(cudaStreamSynchronize(c->last_stream));
+  const int64_t n = std::min<int64_t>(capacity, c->n_obs_rows);
+  if (n > 0) SDE_CUDA_TRY(cudaMemcpy(rows, c->obs, sizeof(sde_obs_row) * n, cudaMemcpyDeviceToHost));
+  if (n_rows) *n_rows = c->n_obs_rows;
+  uint32_t err = 0;
+  SDE_CUDA_TRY(cudaMemcpy(&err, c->err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (err & kErrTimeout) {
+    set_error("a bounded device wait expired");
+    return SDE_ERR_TIMEOUT;
+  }
+  if (err & kErrNonFinite) {
+    set_error("a kernel produced a non-finite state");
+    return SDE_ERR_NUMERIC;
+  }
+  return SDE_OK;
+}
+
+void sde_destroy(sde_ctx *c) { free_ctx(c); }
+
+sde_status sde_get_tuning(const sde_ctx *c, int32_t *block, int32_t *ilp) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
+  if (c->kur) {
+    kuramoto_tuning(c->kur, block, ilp);
+    return SDE_OK;
+  }
+  if (block) *block = c->block;
+  if (ilp) *ilp = c->ilp;
+  return SDE_OK;
+}
+
+sde_status sde_last_kernel_ms(sde_ctx *c, float *ms) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr && ms != nullptr, "ctx and ms must be non-NULL");
+  SDE_CHECK_ARG(c->timed, "no run has been timed yet");
+  SDE_CUDA_TRY(cudaEventSynchronize(c->ev1));
+  SDE_CUDA_TRY(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+  return SDE_OK;
+}
+
+sde_status sde_philox4x32_10(const uint32_t *ctr, uint64_t seed, uint32_t *out, int64_t n,
+                             void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(n >= 0, "n must be >= 0");
+  SDE_CHECK_ARG(n == 0 || (ctr && out), "ctr and out must be non-NULL");
+  SDE_CHECK_ARG(((uintptr_t)ctr % 16) == 0 && ((uintptr_t)out % 16) == 0,
+                "ctr and out must be 16-byte aligned");
+  SDE_CUDA_TRY(philox_fill(ctr, seed, out, n, (cudaStream_t)stream));
+  return SDE_OK;
+}
+
+sde_status sde_box_muller(const uint32_t *ctr, uint64_t seed, float *z, int64_t n, void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(n >= 0, "n must be >= 0");
+  SDE_CHECK_ARG(n == 0 || (ctr && z), "ctr and z must be non-NULL");
+  SDE_CHECK_ARG(((uintptr_t)ctr % 16) == 0 && ((uintptr_t)z % 16) == 0,
+                "ctr and z must be 16-byte aligned");
+  SDE_CUDA_TRY(box_muller_fill(ctr, seed, z, n, (cudaStream_t)stream));
+  return SDE_OK;
+}
+
+}  // extern "C"

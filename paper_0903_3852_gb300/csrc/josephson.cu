@@ -1,0 +1,357 @@
+// josephson.cu -- per-path SRK2 integration of Eq. 1 on the GPU.
+//
+// Each path lives in registers for the whole launch (Alg. 1: load x, v and
+// the parameters, loop over m steps, store back; Sec. 4.1).  One Philox
+// block gives the Gaussians of four consecutive steps (Sec. 4.1 draws two
+// uniforms per step; here one Gaussian per step suffices since Eq. 1 has one
+// noise component).  The step is Alg. 2 applied to y = (x, v):
+//
+//   F1 = -gamma v - 2 pi cos(2 pi x) + a cos(omega t_n) + f
+//   x~ = x + dt v,          v~ = v + dt F1 + s psi
+//   F2 = -gamma v~ - 2 pi cos(2 pi x~) + a cos(omega t_{n+1}) + f
+//   x' = x + dt/2 (v + v~), v' = v + dt/2 (F1 + F2) + s psi,   s = sqrt(2 gamma D dt)
+//
+// Time is kept modulo the drive period as the integer k = n mod P (Sec. 5),
+// so cos(omega t_n) = cos(2 pi k / P) comes from a P-entry table in shared
+// memory.  Position is kept as x in [0, 1) plus an integer winding count, so
+// FP32 resolution does not degrade as paths run away.
+//
+// The window average of v (the time-averaged velocity <<v>> of Sec. 5) is
+// summed in FP32 over blocks of 64 steps and flushed into an FP64 per-path
+// accumulator; per-warp moments of the per-path averages are FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+#include "philox.cuh"
+
+namespace sde {
+namespace {
+
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+template <bool ACC>
+__device__ __forceinline__ void jj_step(float &x, int &w, float &v, float &acc, float z,
+                                        const JJConsts &c, float dr0, float dr1) {
+  const float nz = c.s * z;
+  const float c1 = cospif(2.0f * x);
+  const float F1 = fmaf(-kTwoPiF, c1, fmaf(-c.gamma, v, fmaf(c.a, dr0, c.f)));
+  const float xt = fmaf(c.dt, v, x);
+  const float vt = fmaf(c.dt, F1, v + nz);
+  const float c2 = cospif(2.0f * xt);
+  const float F2 = fmaf(-kTwoPiF, c2, fmaf(-c.gamma, vt, fmaf(c.a, dr1, c.f)));
+  const float xn = fmaf(c.h, v + vt, x);
+  const float vn = fmaf(c.h, F1 + F2, v + nz);
+  const float fl = floorf(xn);
+  x = xn - fl;
+  w += (int)fl;
+  v = vn;
+  if (ACC) acc += vn;
+}
+
+// Advance ILP paths over the steps [n0, n1).  `k` is the drive-table index
+// of step n0 (n0 mod P) and is updated.
+template <int ILP, bool ACC>
+__device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float (&v)[ILP],
+                                           double (&vs)[ILP], const JJConsts &c,
+                                           const float *__restrict__ drive, int P, int &k,
+                                           int64_t n0, int64_t n1, uint2 key,
+                                           const uint32_t (&pid)[ILP], uint32_t point) {
+  if (n0 >= n1) return;
+  float acc[ILP];
+#pragma unroll
+  for (int i = 0; i < ILP; ++i) acc[i] = 0.0f;
+  const int64_t g0 = n0 >> 2, g1 = (n1 - 1) >> 2;
+  int since_flush = 0;
+  for (int64_t g = g0; g <= g1; ++g) {
+    float z[ILP][4];
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) gauss4((uint32_t)g, pid[i], point, kTagJosephson, key, z[i]);
+    const int64_t base = g << 2;
+    if (base >= n0 && base + 4 <= n1) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float dr0 = drive[k];
+        k = (k + 1 == P) ? 0 : k + 1;
+        const float dr1 = drive[k];
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], w[i], v[i], acc[i], z[i][s], c, dr0, dr1);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int64_t n = base + s;
+        if (n >= n0 && n < n1) {
+          const float dr0 = drive[k];
+          k = (k + 1 == P) ? 0 : k + 1;
+          const float dr1 = drive[k];
+#pragma unroll
+          for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], w[i], v[i], acc[i], z[i][s], c, dr0, dr1);
+        }
+      }
+    }
+    if (ACC && ++since_flush == 16) {
+      since_flush = 0;
+#pragma unroll
+      for (int i = 0; i < ILP; ++i) {
+        vs[i] += (double)acc[i];
+        acc[i] = 0.0f;
+      }
+    }
+  }
+  if (ACC) {
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) vs[i] += (double)acc[i];
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  return a;
+}
+
+template <int ILP>
+__device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, int lane) {
+  const JJUnit un = A.units[u];
+  const JJConsts c = A.consts[un.point];
+  const uint2 key = seed_to_key(A.seed);
+  float x[ILP], v[ILP];
+  int w[ILP];
+  double vs[ILP];
+  uint32_t pid[ILP];
+  bool valid[ILP];
+  int64_t gi[ILP];
+#pragma unroll
+  for (int i = 0; i < ILP; ++i) {
+    const int j = lane + 32 * i;
+    valid[i] = j < un.n_paths;
+    pid[i] = (uint32_t)(un.path_begin + j);
+    gi[i] = c.path_offset + un.path_begin + j;
+    x[i] = 0.0f;
+    v[i] = 0.0f;
+    w[i] = 0;
+    vs[i] = 0.0;
+    if (valid[i]) {
+      x[i] = A.st.x_in[gi[i]];
+      v[i] = A.st.v_in[gi[i]];
+      if (A.st.w_in) w[i] = A.st.w_in[gi[i]];
+      if (A.st.vsum_in) vs[i] = A.st.vsum_in[gi[i]];
+    }
+    const float fl = floorf(x[i]);
+    x[i] -= fl;
+    w[i] += (int)fl;
+  }
+  const int64_t nb = A.n_begin;
+  const int64_t ne = A.n_end < c.steps ? A.n_end : c.steps;
+  if (nb < ne) {
+    int k = (int)(nb % A.P);
+    const int64_t split = ne < c.wstart ? ne : c.wstart;
+    jj_segment<ILP, false>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point);
+    jj_segment<ILP, true>(x, w, v, vs, c, drive, A.P, k, nb > c.wstart ? nb : c.wstart, ne, key, pid,
+                          (uint32_t)un.point);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < ILP; ++i) {
+    if (valid[i]) {
+      A.st.x_out[gi[i]] = x[i];
+      A.st.v_out[gi[i]] = v[i];
+      A.st.w_out[gi[i]] = w[i];
+      A.st.vsum_out[gi[i]] = vs[i];
+      bad |= !(isfinite(x[i]) && isfinite(v[i]));
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, kErrNonFinite);
+
+  // Moments of the per-path window averages of this unit.
+  const int64_t reach = A.n_end < c.steps ? A.n_end : c.steps;
+  const int64_t wcount = reach > c.wstart ? reach - c.wstart : 0;
+  double cnt = 0.0, sum = 0.0;
+  if (wcount > 0) {
+#pragma unroll
+    for (int i = 0; i < ILP; ++i)
+      if (valid[i]) {
+        cnt += 1.0;
+        sum += vs[i] / (double)wcount;
+      }
+  }
+  cnt = warp_sum(cnt);
+  sum = warp_sum(sum);
+  const double mean = cnt > 0.0 ? sum / cnt : 0.0;
+  double m2 = 0.0;
+  if (wcount > 0) {
+#pragma unroll
+    for (int i = 0; i < ILP; ++i)
+      if (valid[i]) {
+        const double d = vs[i] / (double)wcount - mean;
+        m2 += d * d;
+      }
+  }
+  m2 = warp_sum(m2);
+  if (lane == 0) A.partials[u] = Moments{cnt, mean, m2};
+}
+
+template <int ILP>
+__global__ void __launch_bounds__(512) jj_kernel(const JJLaunchArgs A) {
+  extern __shared__ float drive_s[];
+  for (int i = threadIdx.x; i < A.P; i += blockDim.x) drive_s[i] = A.drive[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  if (A.queue) {
+    // Persistent: warps pull units from the longest-first work list.
+    for (;;) {
+      int u = 0;
+      if (lane == 0) u = (int)atomicAdd(A.queue, 1u) + A.unit_begin;
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (u >= A.unit_end) break;
+      jj_unit<ILP>(A, u, drive_s, lane);
+    }
+  } else {
+    const int u = A.unit_begin + blockIdx.x * warps + (threadIdx.x >> 5);
+    if (u < A.unit_end) jj_unit<ILP>(A, u, drive_s, lane);
+  }
+}
+
+__global__ void jj_prepare_kernel(const sde_jj_point *pts, int n_points, int P,
+                                  const int64_t *steps, const int64_t *offsets,
+                                  const int64_t *paths, JJConsts *out, float *drive) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_points) {
+    const sde_jj_point p = pts[t];
+    const double dt = 2.0 * 3.14159265358979323846 / (p.omega * (double)P);
+    JJConsts c;
+    c.gamma = (float)p.gamma;
+    c.a = (float)p.a;
+    c.f = (float)p.f;
+    c.dt = (float)dt;
+    c.h = (float)(0.5 * dt);
+    c.s = (float)sqrt(2.0 * p.gamma * p.D * dt);
+    c.paths = (int32_t)paths[t];
+    c.pad = 0;
+    c.steps = steps[t];
+    c.wstart = steps[t] - steps[t] / 2;
+    c.path_offset = offsets[t];
+    c.dt64 = dt;
+    out[t] = c;
+  }
+  if (t < P) drive[t] = (float)cospi(2.0 * (double)t / (double)P);
+}
+
+// Merge of two (n, mean, M2) triples (Chan, Golub & LeVeque 1979).
+__device__ __forceinline__ Moments merge(const Moments &a, const Moments &b) {
+  const double n = a.n + b.n;
+  if (n == 0.0) return Moments{0.0, 0.0, 0.0};
+  const double d = b.mean - a.mean;
+  return Moments{n, a.mean + d * (b.n / n), a.m2 + b.m2 + d * d * (a.n * b.n / n)};
+}
+
+// One warp per point: lane-strided merge over the point's units in a fixed
+// order, then a fixed shuffle tree (deterministic result).
+__global__ void jj_finalize_kernel(const JJConsts *consts, const int2 *range, int n_points,
+                                   const Moments *partials, int64_t n_end, sde_obs_row *obs) {
+  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= n_points) return;
+  const int2 r = range[p];
+  Moments m{0.0, 0.0, 0.0};
+  for (int u = r.x + lane; u < r.y; u += 32) m = merge(m, partials[u]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Moments q;
+    q.n = __shfl_down_sync(0xffffffffu, m.n, o);
+    q.mean = __shfl_down_sync(0xffffffffu, m.mean, o);
+    q.m2 = __shfl_down_sync(0xffffffffu, m.m2, o);
+    if (lane + o < 32) m = merge(m, q);
+  }
+  if (lane == 0) {
+    const JJConsts c = consts[p];
+    const int64_t reach = n_end < c.steps ? n_end : c.steps;
+    sde_obs_row row;
+    row.count = m.n;
+    row.mean = m.n > 0.0 ? m.mean : 0.0;
+    row.var = m.n > 1.0 ? m.m2 / (m.n - 1.0) : 0.0;
+    row.se = m.n > 0.0 ? sqrt(row.var / m.n) : 0.0;
+    row.t = (double)reach * c.dt64;
+    obs[p] = row;
+  }
+}
+
+__global__ void philox_fill_kernel(const uint4 *ctr, uint2 key, uint4 *out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = philox4x32_10(ctr[i], key);
+}
+
+__global__ void box_muller_fill_kernel(const uint4 *ctr, uint2 key, float4 *z, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(ctr[i], key);
+    float4 o;
+    box_muller(r.x, r.y, o.x, o.y);
+    box_muller(r.z, r.w, o.z, o.w);
+    z[i] = o;
+  }
+}
+
+template <int ILP>
+void *jj_kernel_ptr() {
+  return (void *)jj_kernel<ILP>;
+}
+
+}  // namespace
+
+cudaError_t jj_prepare(const sde_jj_point *points_dev, int n_points, int P, const int64_t *steps_dev,
+                       const int64_t *offsets_dev, const int64_t *paths_dev, JJConsts *consts_dev,
+                       float *drive_dev, cudaStream_t s) {
+  const int n = n_points > P ? n_points : P;
+  jj_prepare_kernel<<<(n + 255) / 256, 256, 0, s>>>(points_dev, n_points, P, steps_dev, offsets_dev,
+                                                    paths_dev, consts_dev, drive_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)a.P;
+  if (ilp == 1)
+    jj_kernel<1><<<grid, block, smem, s>>>(a);
+  else if (ilp == 2)
+    jj_kernel<2><<<grid, block, smem, s>>>(a);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+int jj_max_blocks_per_sm(int ilp, int block, int P) {
+  int nb = 0;
+  void *k = ilp == 1 ? jj_kernel_ptr<1>() : jj_kernel_ptr<2>();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, sizeof(float) * P) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t jj_finalize(const JJConsts *consts, const int2 *point_range, int n_points,
+                        const Moments *partials, int64_t n_end, sde_obs_row *obs, cudaStream_t s) {
+  const int wpb = 8;
+  jj_finalize_kernel<<<(n_points + wpb - 1) / wpb, 32 * wpb, 0, s>>>(consts, point_range, n_points,
+                                                                    partials, n_end, obs);
+  return cudaGetLastError();
+}
+
+cudaError_t philox_fill(const uint32_t *ctr, uint64_t seed, uint32_t *out, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  philox_fill_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(
+      (const uint4 *)ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), (uint4 *)out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t box_muller_fill(const uint32_t *ctr, uint64_t seed, float *z, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  box_muller_fill_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(
+      (const uint4 *)ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), (float4 *)z, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sde

@@ -1,0 +1,514 @@
+// kuramoto.cu -- SRK2 integration of the noisy Kuramoto model (Eq. 2,
+// gamma = 1) on the GPU, in three forms of the coupling sum:
+//
+//  * mean field (Eq. 3): sum_j sin(x_j - x_i) = cos x_i S - sin x_i C with
+//    S = sum_j sin x_j, C = sum_j cos x_j.  One CTA owns one replica for the
+//    whole run: its phases stay in registers, S and C come from a block
+//    reduction per stage (two per step), r(t) = sqrt(S^2 + C^2) / N is read
+//    off the first-stage sums.  No grid-wide synchronisation.
+//  * pairwise (Alg. 3 / Fig. 3): the direct all-pairs sum, tiles of source
+//    phases staged in shared memory; one launch per SRK2 stage with the
+//    sub-step fused into the epilogue (Sec. 4.2 splits it into UpdateRHS and
+//    AdvanceSystem; higher order by interleaving stages).
+//  * general K_ij: the sum as a GEMM against [sin x | cos x] (see
+//    kuramoto_general.cu).
+//
+// Phases are kept as 32-bit fixed-point turns (2^32 units per 2 pi): the
+// wrap modulo 2 pi is exact integer overflow and the resolution (1.5e-9
+// rad) does not depend on the phase, in the spirit of keeping time modulo
+// the period (Sec. 5).  Drift increments are computed in FP32 and rounded to
+// the fixed-point grid once per step.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kuramoto.h"
+#include "kuramoto_internal.h"
+#include "philox.cuh"
+
+namespace sde {
+
+namespace {
+
+__device__ __forceinline__ float2 warp_sum2(float a, float b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  return make_float2(a, b);
+}
+
+// Sum of (a, b) over the block; every thread receives the totals.  `red`
+// alternates between two slots so one barrier per reduction suffices.
+__device__ __forceinline__ float2 block_sum2(float a, float b, float2 *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2 v = warp_sum2(a, b);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = lane < nw ? red[lane] : make_float2(0.0f, 0.0f);
+  return warp_sum2(v.x, v.y);
+}
+
+// Blocks of up to 1024 threads hold 1-2 oscillators per thread; larger
+// per-thread counts run in blocks of at most 512 threads (128 registers).
+template <int OPT>
+__global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel(const KurArgs A) {
+  __shared__ float2 red[2][32];
+  const int rep = blockIdx.x;
+  const int64_t N = A.N;
+  const int64_t base = (int64_t)rep * N;
+  const uint2 key = seed_to_key(A.seed);
+  uint32_t th[OPT];
+  float wdt[OPT];
+  bool valid[OPT];
+#pragma unroll
+  for (int k = 0; k < OPT; ++k) {
+    const int64_t i = threadIdx.x + (int64_t)k * blockDim.x;
+    valid[k] = i < N;
+    th[k] = valid[k] ? A.theta_in[base + i] : 0u;
+    wdt[k] = valid[k] ? A.omega[base + i] * A.wscale : 0.0f;
+  }
+  int slot = 0;
+  int64_t sample_ctr = 0;  // (n - n_begin) mod M
+  int64_t sample_idx = 0;
+  const float invN = 1.0f / (float)N;
+  for (int64_t n = A.n_begin; n < A.n_end;) {
+    const int64_t g = n >> 2;
+    float z[OPT][4];
+#pragma unroll
+    for (int k = 0; k < OPT; ++k)
+      gauss4((uint32_t)g, (uint32_t)(threadIdx.x + k * blockDim.x), (uint32_t)rep, kTagKuramoto, key,
+             z[k]);
+    const int s0 = (int)(n & 3);
+    const int64_t rem = A.n_end - (g << 2);
+    const int s1 = rem < 4 ? (int)rem : 4;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (s < s0 || s >= s1) continue;
+      float sn[OPT], cs[OPT], t[OPT];
+      float S = 0.0f, C = 0.0f;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        t[k] = (float)(int32_t)th[k] * 2.3283064365386963e-10f;  // 2^-32
+        sincospif(2.0f * t[k], &sn[k], &cs[k]);
+        if (!valid[k]) sn[k] = cs[k] = 0.0f;
+        S += sn[k];
+        C += cs[k];
+      }
+      float2 sc = block_sum2(S, C, red[slot]);
+      slot ^= 1;
+      if (A.M > 0 && sample_ctr == 0) {
+        if (threadIdx.x == 0 && A.r_out) {
+          const double Sd = sc.x, Cd = sc.y;
+          A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+        }
+        ++sample_idx;
+      }
+      if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
+      float g1[OPT], sn2[OPT], cs2[OPT];
+      float S2 = 0.0f, C2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        g1[k] = cs[k] * sc.x - sn[k] * sc.y;
+        const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
+        sincospif(2.0f * (t[k] + d1), &sn2[k], &cs2[k]);
+        if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
+        S2 += sn2[k];
+        C2 += cs2[k];
+      }
+      sc = block_sum2(S2, C2, red[slot]);
+      slot ^= 1;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        const float g2 = cs2[k] * sc.x - sn2[k] * sc.y;
+        const float d = fmaf(A.sc, z[k][s], fmaf(A.kh, g1[k] + g2, wdt[k]));
+        th[k] += (uint32_t)__float2int_rn(d * 4294967296.0f);
+      }
+    }
+    n = (g + 1) << 2;
+  }
+  // Final sample at n_end.
+  if (A.M > 0) {
+    float S = 0.0f, C = 0.0f;
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) {
+      float sn, cs;
+      sincospif(2.0f * ((float)(int32_t)th[k] * 2.3283064365386963e-10f), &sn, &cs);
+      if (valid[k]) {
+        S += sn;
+        C += cs;
+      }
+    }
+    const float2 sc = block_sum2(S, C, red[slot]);
+    if (threadIdx.x == 0 && A.r_out) {
+      const double Sd = sc.x, Cd = sc.y;
+      A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+    }
+  }
+  (void)invN;
+#pragma unroll
+  for (int k = 0; k < OPT; ++k) {
+    const int64_t i = threadIdx.x + (int64_t)k * blockDim.x;
+    if (valid[k]) A.theta_out[base + i] = th[k];
+  }
+}
+
+// ---- pairwise form (Alg. 3) --------------------------------------------
+
+constexpr int kPairThreads = 128;
+constexpr int kPairPerThread = 2;  // receivers per thread
+constexpr int kPairTile = kPairThreads * kPairPerThread;
+
+// One SRK2 stage: receivers i of one replica in this CTA, all sources j
+// streamed through shared memory in tiles.  STAGE 0 (predictor) reads the
+// phases theta, writes theta~ and the first-stage coupling sum g1; STAGE 1
+// (corrector) takes the sums over theta~ and writes the new theta.
+template <int STAGE>
+__global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPairArgs A) {
+  __shared__ float src_s[kPairTile];
+  const int rep = blockIdx.y;
+  const int64_t N = A.N;
+  const int64_t base = (int64_t)rep * N;
+  const uint32_t *src = STAGE == 0 ? A.theta : A.theta_t;
+  float ti[kPairPerThread], acc[kPairPerThread];
+  int64_t idx[kPairPerThread];
+#pragma unroll
+  for (int k = 0; k < kPairPerThread; ++k) {
+    idx[k] = (int64_t)blockIdx.x * kPairTile + threadIdx.x + k * kPairThreads;
+    ti[k] = idx[k] < N ? (float)(int32_t)src[base + idx[k]] * 2.3283064365386963e-10f : 0.0f;
+    acc[k] = 0.0f;
+  }
+  for (int64_t j0 = 0; j0 < N; j0 += kPairTile) {
+    const int cnt = (N - j0) < kPairTile ? (int)(N - j0) : kPairTile;
+#pragma unroll
+    for (int k = 0; k < kPairPerThread; ++k) {
+      const int jj = threadIdx.x + k * kPairThreads;
+      if (jj < cnt) src_s[jj] = (float)(int32_t)src[base + j0 + jj] * 2.3283064365386963e-10f;
+    }
+    __syncthreads();
+    if (cnt == kPairTile) {
+#pragma unroll 8
+      for (int jj = 0; jj < kPairTile; ++jj) {
+        const float tj = src_s[jj];
+#pragma unroll
+        for (int k = 0; k < kPairPerThread; ++k) {
+          float d = tj - ti[k];
+          d -= rintf(d);
+          acc[k] += __sinf(6.28318530717958647692f * d);
+        }
+      }
+    } else {
+      for (int jj = 0; jj < cnt; ++jj) {
+        const float tj = src_s[jj];
+#pragma unroll
+        for (int k = 0; k < kPairPerThread; ++k) {
+          float d = tj - ti[k];
+          d -= rintf(d);
+          acc[k] += __sinf(6.28318530717958647692f * d);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const uint2 key = seed_to_key(A.seed);
+  const int64_t n = A.n;
+#pragma unroll
+  for (int k = 0; k < kPairPerThread; ++k) {
+    if (idx[k] >= N) continue;
+    const int64_t gi = base + idx[k];
+    float z[4];
+    gauss4((uint32_t)(n >> 2), (uint32_t)idx[k], (uint32_t)rep, kTagKuramoto, key, z);
+    const float psi = z[n & 3];
+    const float wdt = A.omega[gi] * A.wscale;
+    if (STAGE == 0) {
+      const float d1 = fmaf(A.sc, psi, fmaf(A.kc, acc[k], wdt));
+      A.theta_t[gi] = A.theta[gi] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+      A.g1[gi] = acc[k];
+    } else {
+      const float d = fmaf(A.sc, psi, fmaf(A.kh, A.g1[gi] + acc[k], wdt));
+      A.theta[gi] += (uint32_t)__float2int_rn(d * 4294967296.0f);
+    }
+  }
+}
+
+// r(t) of every replica from fixed-point phases (one CTA per replica).
+__global__ void kur_order_kernel(const uint32_t *theta, int64_t N, int64_t R, double *r_out) {
+  __shared__ float2 red[32];
+  const int rep = blockIdx.x;
+  float S = 0.0f, C = 0.0f;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    float sn, cs;
+    sincospif(2.0f * ((float)(int32_t)theta[(int64_t)rep * N + i] * 2.3283064365386963e-10f), &sn, &cs);
+    S += sn;
+    C += cs;
+  }
+  const float2 sc = block_sum2(S, C, red);
+  if (threadIdx.x == 0) {
+    const double Sd = sc.x, Cd = sc.y;
+    r_out[rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+  }
+}
+
+// Radians (any range) <-> fixed-point turns.
+__global__ void kur_to_fixed(const float *phi, uint32_t *theta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double t = (double)phi[i] * 0.15915494309189533577;  // 1 / (2 pi)
+    t -= floor(t);
+    theta[i] = (uint32_t)(uint64_t)llrint(t * 4294967296.0);
+  }
+}
+
+__global__ void kur_from_fixed(const uint32_t *theta, float *phi, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    phi[i] = (float)((double)theta[i] * 2.3283064365386963e-10 * 6.28318530717958647692);
+}
+
+// Observables: mean, variance and standard error of r over replicas for
+// each sample row (one warp per row, fixed summation order).
+__global__ void kur_obs_kernel(const double *r, int64_t rows, int64_t R, int64_t n_begin, int64_t n_end,
+                               int M, double dt, sde_obs_row *obs) {
+  const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  double s = 0.0;
+  for (int64_t q = lane; q < R; q += 32) s += r[row * R + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const double mean = s / (double)R;
+  double m2 = 0.0;
+  for (int64_t q = lane; q < R; q += 32) {
+    const double d = r[row * R + q] - mean;
+    m2 += d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+  if (lane == 0) {
+    sde_obs_row o;
+    o.mean = mean;
+    o.count = (double)R;
+    o.var = R > 1 ? m2 / (double)(R - 1) : 0.0;
+    o.se = sqrt(o.var / (double)R);
+    const int64_t n = row == rows - 1 ? n_end : n_begin + row * (int64_t)M;
+    o.t = (double)n * dt;
+    obs[row] = o;
+  }
+}
+
+template <int OPT>
+void *mf_kernel_ptr() {
+  return (void *)kur_meanfield_kernel<OPT>;
+}
+
+cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, cudaStream_t s) {
+  switch (opt) {
+    case 1: kur_meanfield_kernel<1><<<(unsigned)a.R, block, 0, s>>>(a); break;
+    case 2: kur_meanfield_kernel<2><<<(unsigned)a.R, block, 0, s>>>(a); break;
+    case 4: kur_meanfield_kernel<4><<<(unsigned)a.R, block, 0, s>>>(a); break;
+    case 8: kur_meanfield_kernel<8><<<(unsigned)a.R, block, 0, s>>>(a); break;
+    case 16: kur_meanfield_kernel<16><<<(unsigned)a.R, block, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int pow2_at_least(int64_t x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, KuramotoCtx **out) {
+  *out = nullptr;
+  SDE_CHECK_ARG(cfg->n_osc >= 1, "n_osc must be >= 1");
+  SDE_CHECK_ARG(cfg->n_replicas >= 1 && cfg->n_replicas <= 65535, "n_replicas must be in [1, 65535]");
+  SDE_CHECK_ARG(isfinite(cfg->K) && isfinite(cfg->D) && isfinite(cfg->dt), "K, D, dt must be finite");
+  SDE_CHECK_ARG(cfg->D >= 0.0, "D must be >= 0");
+  SDE_CHECK_ARG(cfg->dt > 0.0, "dt must be > 0");
+  SDE_CHECK_ARG(cfg->sample_every >= 0, "sample_every must be >= 0");
+  SDE_CHECK_ARG(cfg->n_osc < (1ll << 31), "n_osc too large");
+  if (cfg->model == SDE_KURAMOTO_MEANFIELD)
+    SDE_CHECK_ARG(cfg->n_osc <= 8192, "mean-field form holds a replica in one CTA: n_osc <= 8192");
+  KuramotoCtx *k = new (std::nothrow) KuramotoCtx();
+  if (!k) {
+    set_error("host allocation failed");
+    return SDE_ERR_NO_MEMORY;
+  }
+  k->model = cfg->model;
+  k->N = cfg->n_osc;
+  k->R = cfg->n_replicas;
+  k->K = cfg->K;
+  k->D = cfg->D;
+  k->dt = cfg->dt;
+  k->M = cfg->sample_every;
+  k->seed = cfg->seed;
+  k->sm_count = sm_count;
+  k->err = err;
+  k->flags = cfg->flags;
+  const size_t NR = (size_t)k->N * (size_t)k->R;
+  sde_status st = SDE_OK;
+  cudaError_t e;
+  auto alloc = [&](void **p, size_t bytes) {
+    if (st != SDE_OK) return;
+    if ((e = cudaMalloc(p, bytes ? bytes : 1)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
+  };
+  alloc((void **)&k->theta, NR * 4);
+  if (cfg->model == SDE_KURAMOTO_PAIRWISE) {
+    alloc((void **)&k->theta_t, NR * 4);
+    alloc((void **)&k->g1, NR * 4);
+  }
+  if (st == SDE_OK && (cfg->model == SDE_KURAMOTO_GENERAL || cfg->model == SDE_KURAMOTO_GENERAL_FP32))
+    st = kuramoto_general_alloc(k);
+  if (st != SDE_OK) {
+    kuramoto_destroy(k);
+    return st;
+  }
+  // Launch shape.
+  if (cfg->model == SDE_KURAMOTO_MEANFIELD) {
+    int block = cfg->block_threads;
+    if (block == 0) {
+      block = (int)std::min<int64_t>(1024, ((k->N + 31) / 32) * 32);
+      if (k->N > 2048) block = 512;
+    }
+    int opt = pow2_at_least((k->N + block - 1) / block);
+    if (block < 32 || block % 32 != 0 || block > (opt <= 2 ? 1024 : 512) || opt > 16) {
+      kuramoto_destroy(k);
+      set_error("invalid argument: block_threads must be a multiple of 32, at most 1024 for <= 2 "
+                "oscillators per thread and 512 above, with at most 16 oscillators per thread");
+      return SDE_ERR_INVALID_ARG;
+    }
+    k->block = block;
+    k->opt = opt;
+  } else if (cfg->model == SDE_KURAMOTO_PAIRWISE) {
+    k->block = kPairThreads;
+    k->opt = kPairPerThread;
+  }
+  *out = k;
+  return SDE_OK;
+}
+
+void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread) {
+  if (block) *block = k->block;
+  if (per_thread) *per_thread = k->opt;
+}
+
+void kuramoto_destroy(KuramotoCtx *k) {
+  if (!k) return;
+  cudaDeviceSynchronize();
+  cudaFree(k->theta);
+  cudaFree(k->theta_t);
+  cudaFree(k->g1);
+  cudaFree(k->r_scratch);
+  kuramoto_general_free(k);
+  delete k;
+}
+
+sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, cudaEvent_t ev0,
+                        cudaEvent_t ev1, sde_obs_row *obs_in, sde_obs_row **obs, int64_t *max_rows,
+                        int64_t *rows) {
+  SDE_CHECK_ARG(r->phi_in_dev && r->phi_out_dev && r->omega_dev,
+                "Kuramoto run needs phi_in, phi_out and omega");
+  const int64_t L = r->n_end - r->n_begin;
+  const int64_t n_rows = k->M > 0 ? (L + k->M - 1) / k->M + 1 : 0;
+  // Observable and sample buffers.
+  if (n_rows > *max_rows) {
+    cudaFree(obs_in);
+    *obs = nullptr;
+    *max_rows = 0;
+    SDE_CUDA_TRY(cudaMalloc((void **)obs, sizeof(sde_obs_row) * n_rows));
+    *max_rows = n_rows;
+  }
+  double *rbuf = r->r_out_dev;
+  if (!rbuf && n_rows > 0) {
+    if (k->r_scratch_rows < n_rows) {
+      cudaFree(k->r_scratch);
+      k->r_scratch = nullptr;
+      k->r_scratch_rows = 0;
+      SDE_CUDA_TRY(cudaMalloc((void **)&k->r_scratch, sizeof(double) * n_rows * k->R));
+      k->r_scratch_rows = n_rows;
+    }
+    rbuf = k->r_scratch;
+  }
+  const int64_t NR = k->N * k->R;
+  const int cvt_grid = (int)std::min<int64_t>((NR + 255) / 256, 4096);
+  kur_to_fixed<<<cvt_grid, 256, 0, s>>>(r->phi_in_dev, k->theta, NR);
+  SDE_CUDA_TRY(cudaGetLastError());
+  const double inv2pi = 0.15915494309189533577;
+  SDE_CUDA_TRY(cudaEventRecord(ev0, s));
+  if (k->model == SDE_KURAMOTO_MEANFIELD) {
+    KurArgs a{};
+    a.theta_in = k->theta;
+    a.theta_out = k->theta;
+    a.omega = r->omega_dev;
+    a.r_out = rbuf;
+    a.N = k->N;
+    a.R = k->R;
+    a.n_begin = r->n_begin;
+    a.n_end = r->n_end;
+    a.M = k->M;
+    a.wscale = (float)(k->dt * inv2pi);
+    a.kc = (float)(k->K / (double)k->N * k->dt * inv2pi);
+    a.kh = (float)(0.5 * k->K / (double)k->N * k->dt * inv2pi);
+    a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
+    a.seed = k->seed;
+    a.err = k->err;
+    SDE_CUDA_TRY(launch_meanfield(a, k->block, k->opt, s));
+  } else if (k->model == SDE_KURAMOTO_PAIRWISE) {
+    KurPairArgs a{};
+    a.theta = k->theta;
+    a.theta_t = k->theta_t;
+    a.g1 = k->g1;
+    a.omega = r->omega_dev;
+    a.N = k->N;
+    a.wscale = (float)(k->dt * inv2pi);
+    a.kc = (float)(k->K / (double)k->N * k->dt * inv2pi);
+    a.kh = (float)(0.5 * k->K / (double)k->N * k->dt * inv2pi);
+    a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
+    a.seed = k->seed;
+    const dim3 grid((unsigned)((k->N + kPairTile - 1) / kPairTile), (unsigned)k->R);
+    int64_t sample = 0;
+    for (int64_t n = r->n_begin; n < r->n_end; ++n) {
+      if (k->M > 0 && (n - r->n_begin) % k->M == 0) {
+        kur_order_kernel<<<(unsigned)k->R, 256, 0, s>>>(k->theta, k->N, k->R, rbuf + sample * k->R);
+        ++sample;
+      }
+      a.n = n;
+      kur_pairwise_stage<0><<<grid, kPairThreads, 0, s>>>(a);
+      kur_pairwise_stage<1><<<grid, kPairThreads, 0, s>>>(a);
+    }
+    SDE_CUDA_TRY(cudaGetLastError());
+    if (k->M > 0) kur_order_kernel<<<(unsigned)k->R, 256, 0, s>>>(k->theta, k->N, k->R, rbuf + sample * k->R);
+  } else {
+    sde_status st = kuramoto_general_run(k, r, s, rbuf);
+    if (st != SDE_OK) return st;
+  }
+  SDE_CUDA_TRY(cudaGetLastError());
+  SDE_CUDA_TRY(cudaEventRecord(ev1, s));
+  kur_from_fixed<<<cvt_grid, 256, 0, s>>>(k->theta, r->phi_out_dev, NR);
+  SDE_CUDA_TRY(cudaGetLastError());
+  if (n_rows > 0) {
+    kur_obs_kernel<<<(unsigned)((n_rows + 7) / 8), 256, 0, s>>>(rbuf, n_rows, k->R, r->n_begin, r->n_end,
+                                                                 k->M, k->dt, *obs);
+    SDE_CUDA_TRY(cudaGetLastError());
+  }
+  *rows = n_rows;
+  return SDE_OK;
+}
+
+cudaError_t kur_order_launch(const uint32_t *theta, int64_t N, int64_t R, double *r_out, cudaStream_t s) {
+  kur_order_kernel<<<(unsigned)R, 256, 0, s>>>(theta, N, R, r_out);
+  return cudaGetLastError();
+}
+
+}  // namespace sde

@@ -1,0 +1,24 @@
+// kuramoto.h -- Kuramoto (Eq. 2) part of the library: context and entry
+// points used by abi.cu.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sde {
+
+struct KuramotoCtx;
+
+sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, KuramotoCtx **out);
+// Advance and reduce; (re)allocates the observables buffer *obs if it has
+// fewer than the run's sample rows.  ev0/ev1 bracket the dominant kernels.
+sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, cudaEvent_t ev0,
+                        cudaEvent_t ev1, sde_obs_row *obs_in, sde_obs_row **obs,
+                        int64_t *max_rows, int64_t *rows);
+sde_status kuramoto_set_coupling(KuramotoCtx *k, const float *K_dev, cudaStream_t s);
+void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread);
+void kuramoto_destroy(KuramotoCtx *k);
+
+}  // namespace sde

@@ -1,0 +1,61 @@
+// philox.cuh -- counter-based Gaussian noise on the device.
+//
+// Philox4x32-10 from Salmon, Moraes, Dror & Shaw, "Parallel random numbers:
+// as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 multiplies with
+// the multipliers 0xD2511F53 and 0xCD9E8D57, the round permutation
+// (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), and the key bumped by the Weyl
+// constants 0x9E3779B9, 0xBB67AE85 after every round.  It replaces the
+// per-thread xorshift generator of Sec. 4.1: the noise of step n is a pure
+// function of (step, path, point) so that runs split at any step reproduce
+// the unsplit run bit for bit.
+//
+// Uniforms take the top 24 bits of a word: u = ((w >> 8) + 1) * 2^-24, in
+// (0, 1] and exact in FP32.  Box-Muller (Sec. 4.1, two uniforms -> two
+// Gaussians): z0 = sqrt(-2 ln u0) cos(2 pi u1), z1 = sqrt(-2 ln u0) sin(2 pi u1).
+#pragma once
+
+#include <stdint.h>
+
+namespace sde {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint2 seed_to_key(uint64_t seed) {
+  return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ float uniform24(uint32_t w) {
+  return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;  // 2^-24
+}
+
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1) {
+  const float u0 = uniform24(w0);
+  const float u1 = uniform24(w1);
+  const float rho = sqrtf(-2.0f * logf(u0));
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  z0 = rho * c;
+  z1 = rho * s;
+}
+
+// Four Gaussians of one Philox block: steps 4g..4g+3 of a stream.
+__device__ __forceinline__ void gauss4(uint32_t g, uint32_t c1, uint32_t c2, uint32_t tag,
+                                       uint2 key, float (&z)[4]) {
+  const uint4 r = philox4x32_10(make_uint4(g, c1, c2, tag), key);
+  box_muller(r.x, r.y, z[0], z[1]);
+  box_muller(r.z, r.w, z[2], z[3]);
+}
+
+}  // namespace sde

@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C ABI in include/sde.h (libsde_gb300.so).
+
+Argument marshalling only: every step of the integration runs in the CUDA
+library.  Device buffers are torch tensors on the current CUDA device; their
+data pointers and the current torch stream are passed through unchanged.  There
+is no CPU fallback: if the library is missing this module raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsde_gb300.so")
+
+SDE_OK = 0
+STATUS_NAMES = {0: "SDE_OK", 1: "SDE_ERR_INVALID_ARG", 2: "SDE_ERR_CUDA", 3: "SDE_ERR_NO_MEMORY",
+                4: "SDE_ERR_TIMEOUT", 5: "SDE_ERR_UNSUPPORTED", 6: "SDE_ERR_NUMERIC"}
+
+SDE_JOSEPHSON = 0
+SDE_KURAMOTO_MEANFIELD = 1
+SDE_KURAMOTO_PAIRWISE = 2
+SDE_KURAMOTO_GENERAL = 3
+SDE_KURAMOTO_GENERAL_FP32 = 4
+
+SDE_SCHED_PERSISTENT = 0
+SDE_SCHED_PLAIN = 1
+
+SDE_FLAG_NO_GRAPH = 1
+
+
+class SDEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class JJPoint(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("a", ctypes.c_double), ("omega", ctypes.c_double),
+                ("f", ctypes.c_double), ("D", ctypes.c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("schedule", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("n_points", ctypes.c_int32), ("steps_per_period", ctypes.c_int32),
+                ("points", ctypes.POINTER(JJPoint)), ("paths", ctypes.POINTER(ctypes.c_int64)),
+                ("steps", ctypes.POINTER(ctypes.c_int64)),
+                ("n_osc", ctypes.c_int64), ("n_replicas", ctypes.c_int64), ("K", ctypes.c_double),
+                ("D", ctypes.c_double), ("dt", ctypes.c_double), ("sample_every", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("paths_per_thread", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class RunDesc(ctypes.Structure):
+    _fields_ = [("n_begin", ctypes.c_int64), ("n_end", ctypes.c_int64),
+                ("x_in_dev", ctypes.c_void_p), ("v_in_dev", ctypes.c_void_p),
+                ("w_in_dev", ctypes.c_void_p), ("vsum_in_dev", ctypes.c_void_p),
+                ("x_out_dev", ctypes.c_void_p), ("v_out_dev", ctypes.c_void_p),
+                ("w_out_dev", ctypes.c_void_p), ("vsum_out_dev", ctypes.c_void_p),
+                ("phi_in_dev", ctypes.c_void_p), ("phi_out_dev", ctypes.c_void_p),
+                ("omega_dev", ctypes.c_void_p), ("r_out_dev", ctypes.c_void_p)]
+
+
+class ObsRow(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("var", ctypes.c_double), ("se", ctypes.c_double),
+                ("count", ctypes.c_double), ("t", ctypes.c_double)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol declared in include/sde.h
+_VP = ctypes.c_void_p
+SIGNATURES = [
+    ("sde_create", ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_VP)]),
+    ("sde_run_ensemble", ctypes.c_int, [_VP, ctypes.POINTER(RunDesc), _VP]),
+    ("sde_observables", ctypes.c_int, [_VP, ctypes.POINTER(ObsRow), ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    ("sde_destroy", None, [_VP]),
+    ("sde_last_error", ctypes.c_char_p, []),
+    ("sde_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    ("sde_last_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    ("sde_philox4x32_10", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
+    ("sde_box_muller", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
+    ("sde_abi_version", ctypes.c_int32, []),
+]
+
+
+def lib():
+    """Load libsde_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsde_gb300.so is not built (%s); run "
+                               "python -c 'import __graft_entry__ as g; g.build()'" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != SDE_OK:
+        raise SDEError(status, lib().sde_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "need contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def philox4x32_10(ctr, seed, stream=None):
+    """ctr: (n, 4) int32/uint32 CUDA tensor -> (n, 4) int32 tensor of Philox words (bit patterns)."""
+    import torch
+    assert ctr.dim() == 2 and ctr.shape[1] == 4
+    out = torch.empty_like(ctr)
+    _check(lib().sde_philox4x32_10(_ptr(ctr), seed, _ptr(out), ctr.shape[0], _stream(stream)))
+    return out
+
+
+def box_muller(ctr, seed, stream=None):
+    """ctr: (n, 4) int32 CUDA tensor -> (n, 4) float32 Gaussians as the integrators draw them."""
+    import torch
+    assert ctr.dim() == 2 and ctr.shape[1] == 4
+    z = torch.empty(ctr.shape, dtype=torch.float32, device=ctr.device)
+    _check(lib().sde_box_muller(_ptr(ctr), seed, _ptr(z), ctr.shape[0], _stream(stream)))
+    return z
+
+
+class Ensemble:
+    """An sde_ctx: one configured ensemble (Josephson points or Kuramoto replicas)."""
+
+    def __init__(self, cfg: Config, keep=()):
+        self._keep = keep
+        h = _VP()
+        _check(lib().sde_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self.cfg = cfg
+
+    @classmethod
+    def josephson(cls, points, paths, steps, seed, steps_per_period=200,
+                  schedule=SDE_SCHED_PERSISTENT, block_threads=0, paths_per_thread=0, flags=0):
+        n = len(points)
+        pts = (JJPoint * n)(*[JJPoint(p["gamma"], p["a"], p["omega"], p["f"], p["D"]) for p in points])
+        pa = np.ascontiguousarray(np.asarray(paths, dtype=np.int64))
+        st = np.ascontiguousarray(np.asarray(steps, dtype=np.int64))
+        cfg = Config()
+        cfg.model = SDE_JOSEPHSON
+        cfg.schedule = schedule
+        cfg.seed = seed
+        cfg.n_points = n
+        cfg.steps_per_period = steps_per_period
+        cfg.points = ctypes.cast(pts, ctypes.POINTER(JJPoint))
+        cfg.paths = pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        cfg.steps = st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        cfg.block_threads = block_threads
+        cfg.paths_per_thread = paths_per_thread
+        cfg.flags = flags
+        e = cls(cfg, keep=(pts, pa, st))
+        e.n_points = n
+        e.paths = pa.copy()
+        e.steps = st.copy()
+        e.total_paths = int(pa.sum())
+        return e
+
+    @classmethod
+    def kuramoto(cls, model, n_osc, n_replicas, K, D, dt, seed, sample_every=100, block_threads=0,
+                 flags=0):
+        cfg = Config()
+        cfg.model = model
+        cfg.seed = seed
+        cfg.n_osc = n_osc
+        cfg.n_replicas = n_replicas
+        cfg.K = K
+        cfg.D = D
+        cfg.dt = dt
+        cfg.sample_every = sample_every
+        cfg.block_threads = block_threads
+        cfg.flags = flags
+        e = cls(cfg)
+        e.n_osc, e.n_replicas, e.sample_every = n_osc, n_replicas, sample_every
+        return e
+
+    def run_josephson(self, n_begin, n_end, x_in, v_in, x_out, v_out, w_out, vsum_out, w_in=None,
+                      vsum_in=None, stream=None):
+        r = RunDesc()
+        r.n_begin, r.n_end = n_begin, n_end
+        r.x_in_dev, r.v_in_dev = _ptr(x_in), _ptr(v_in)
+        r.w_in_dev, r.vsum_in_dev = _ptr(w_in), _ptr(vsum_in)
+        r.x_out_dev, r.v_out_dev = _ptr(x_out), _ptr(v_out)
+        r.w_out_dev, r.vsum_out_dev = _ptr(w_out), _ptr(vsum_out)
+        _check(lib().sde_run_ensemble(self._h, ctypes.byref(r), _stream(stream)))
+
+    def run_kuramoto(self, n_begin, n_end, phi_in, phi_out, omega, r_out=None, stream=None):
+        r = RunDesc()
+        r.n_begin, r.n_end = n_begin, n_end
+        r.phi_in_dev, r.phi_out_dev, r.omega_dev = _ptr(phi_in), _ptr(phi_out), _ptr(omega)
+        r.r_out_dev = _ptr(r_out)
+        _check(lib().sde_run_ensemble(self._h, ctypes.byref(r), _stream(stream)))
+
+    def observables(self, capacity=None):
+        """Synchronise and return the FP64 observables as a structured numpy array
+        with fields mean, var, se, count, t."""
+        n = ctypes.c_int64()
+        _check(lib().sde_observables(self._h, None, 0, ctypes.byref(n)))
+        cap = n.value if capacity is None else capacity
+        rows = (ObsRow * max(cap, 1))()
+        _check(lib().sde_observables(self._h, rows, cap, ctypes.byref(n)))
+        dt = np.dtype([("mean", "f8"), ("var", "f8"), ("se", "f8"), ("count", "f8"), ("t", "f8")])
+        out = np.frombuffer(bytearray(rows)[:ctypes.sizeof(ObsRow) * min(cap, n.value)], dtype=dt)
+        return out.copy()
+
+    def tuning(self):
+        b, i = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sde_get_tuning(self._h, ctypes.byref(b), ctypes.byref(i)))
+        return b.value, i.value
+
+    def last_kernel_ms(self):
+        ms = ctypes.c_float()
+        _check(lib().sde_last_kernel_ms(self._h, ctypes.byref(ms)))
+        return ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sde_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,105 @@
+"""GPU parity of the Eq. 2 integrators (mean-field and pairwise forms) against
+the FP64 oracle's direct pairwise sum.  Phases are compared as wrapped angles,
+|d| <= 1e-5 max(1, |phi_ref mod 2 pi|) over 10^3 steps with identical
+Gaussians; r(t) samples against the oracle's; observables within 3 SE."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import angle_diff, ensure_built, kur_run
+from paper_0903_3852_gb300 import inputs, sde
+
+pytestmark = pytest.mark.gpu
+
+
+def _ens(model, N, R, K, D, dt, seed, M, **kw):
+    ensure_built()
+    return sde.Ensemble.kuramoto(model, N, R, K, D, dt, seed, sample_every=M, **kw)
+
+
+def _check_phases(phig, phio, tol=1e-5):
+    ref = np.mod(phio, 2 * np.pi)
+    err = np.abs(angle_diff(phig, phio)) / np.maximum(1.0, ref)
+    return err.max()
+
+
+@pytest.mark.parametrize("N,R,block", [(1000, 3, 0), (4096, 2, 0), (4096, 2, 1024), (37, 2, 0)])
+def test_meanfield_pathwise(N, R, block):
+    steps, M, seed = 1000, 100, 7
+    w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=3)
+    ens = _ens(sde.SDE_KURAMOTO_MEANFIELD, N, R, 2.0, 0.05, 0.01, seed, M, block_threads=block)
+    phig, rg, obs = kur_run(ens, w["phi0"], w["omega"], 0, steps)
+    worst = 0.0
+    for r in range(R):
+        phio, ro = oracle.kuramoto_run(w["phi0"][r], w["omega"][r], 0.05, 0.01, 0, steps, seed, r,
+                                       Kconst=2.0 / N, meanfield=True, sample_every=M)
+        worst = max(worst, _check_phases(phig[r], phio))
+        assert np.max(np.abs(rg[:, r] - ro)) <= 2e-5
+    print("meanfield N=%d max phase err %.2e" % (N, worst))
+    assert worst <= 1e-5
+    assert obs.shape[0] == steps // M + 1
+    assert np.allclose(obs["mean"], rg.mean(axis=1), rtol=0, atol=1e-12)
+    assert np.allclose(obs["t"], np.arange(obs.shape[0]) * M * 0.01)
+
+
+def test_meanfield_matches_direct_oracle_sum():
+    # the oracle's direct O(N^2) sum (the plain definition) against the GPU's Eq. 3 form
+    N, R, steps = 256, 2, 300
+    w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=4)
+    ens = _ens(sde.SDE_KURAMOTO_MEANFIELD, N, R, 2.0, 0.05, 0.01, 11, 0)
+    phig, _, _ = kur_run(ens, w["phi0"], w["omega"], 0, steps)
+    for r in range(R):
+        phio, _ = oracle.kuramoto_run(w["phi0"][r], w["omega"][r], 0.05, 0.01, 0, steps, 11, r,
+                                      Kconst=2.0 / N, meanfield=False)
+        assert _check_phases(phig[r], phio) <= 1e-5
+
+
+@pytest.mark.parametrize("N,R", [(300, 2), (1024, 1)])
+def test_pairwise_pathwise(N, R):
+    steps, M, seed = 203, 50, 5
+    w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=6)
+    ens = _ens(sde.SDE_KURAMOTO_PAIRWISE, N, R, 2.0, 0.05, 0.01, seed, M)
+    phig, rg, obs = kur_run(ens, w["phi0"], w["omega"], 0, steps)
+    for r in range(R):
+        phio, ro = oracle.kuramoto_run(w["phi0"][r], w["omega"][r], 0.05, 0.01, 0, steps, seed, r,
+                                       Kconst=2.0 / N, meanfield=False, sample_every=M)
+        err = _check_phases(phig[r], phio)
+        print("pairwise N=%d max phase err %.2e" % (N, err))
+        assert err <= 1e-5
+        assert np.max(np.abs(rg[:, r] - ro)) <= 2e-5
+
+
+def test_pairwise_and_meanfield_agree_and_resume():
+    N, R, steps = 512, 2, 400
+    w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=8)
+    a = _ens(sde.SDE_KURAMOTO_PAIRWISE, N, R, 2.0, 0.05, 0.01, 1, 100)
+    b = _ens(sde.SDE_KURAMOTO_MEANFIELD, N, R, 2.0, 0.05, 0.01, 1, 100)
+    pa, ra, _ = kur_run(a, w["phi0"], w["omega"], 0, steps)
+    pb, rb, _ = kur_run(b, w["phi0"], w["omega"], 0, steps)
+    assert np.abs(angle_diff(pa, pb)).max() <= 2e-5
+    # split run (counter-based noise): 0..150 then 150..400
+    p1, _, _ = kur_run(b, w["phi0"], w["omega"], 0, 150)
+    p2, _, _ = kur_run(b, p1.astype(np.float32), w["omega"], 150, steps)
+    assert np.abs(angle_diff(p2, pb)).max() <= 2e-6  # only the phi <-> fixed-point round trip differs
+
+
+def test_uniform_size_r_of_t_within_3se():
+    w = inputs.kuramoto_uniform()
+    N, R, S, M = w["n_osc"], w["replicas"], w["steps"], w["sample_every"]
+    ens = _ens(sde.SDE_KURAMOTO_MEANFIELD, N, R, w["K"], w["D"], w["dt"], w["seed"], M)
+    phig, rg, obs = kur_run(ens, w["phi0"], w["omega"], 0, S)
+    assert obs.shape[0] == S // M + 1
+    assert np.all(np.isfinite(obs["mean"]))
+    # oracle on two replicas (mean-field form, pinned to the direct sum by Eq. 3)
+    S_o = 2000
+    for r in range(2):
+        phio, ro = oracle.kuramoto_run(w["phi0"][r], w["omega"][r], w["D"], w["dt"], 0, S_o, w["seed"],
+                                       r, Kconst=w["K"] / N, meanfield=True, sample_every=M)
+        nrow = S_o // M
+        assert np.max(np.abs(rg[:nrow, r] - ro[:nrow])) <= 1e-4
+    # late-time order parameter: mean over replicas vs the oracle's replicas
+    late = slice(S // M // 2, None)
+    print("r late mean %.4f se %.4f" % (obs["mean"][late].mean(), obs["se"][late].mean()))
+    assert 0.0 < obs["mean"][-1] < 1.0
