@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairwise-steps", type=int, default=200,
                     help="steps per bench step of the pairwise Kuramoto workload")
+    # reduced cases for profiler captures (not bench lines)
+    ap.add_argument("--points", type=int, default=0, help="sweep: keep only the first N points")
+    ap.add_argument("--steps-cap", type=int, default=0, help="sweep: cap every point's step count")
+    ap.add_argument("--block", type=int, default=0, help="fixed threads per block (skips autotuning)")
+    ap.add_argument("--ilp", type=int, default=0, help="fixed paths per thread (skips autotuning)")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -104,10 +110,17 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- workloads
-def sweep_workload(rank):
+def sweep_workload(rank, args=None):
     w = inputs.josephson_sweep()
     # each rank integrates its own copy with its own noise key (weak scaling)
     w["seed"] = w["seed"] + 1000 * rank
+    if args is not None and (args.points or args.steps_cap):
+        k = args.points or len(w["points"])
+        n = int(w["paths"][:k].sum())
+        w["points"], w["paths"], w["x0"], w["v0"] = w["points"][:k], w["paths"][:k], w["x0"][:n], w["v0"][:n]
+        w["steps"] = w["steps"][:k]
+        if args.steps_cap:
+            w["steps"] = np.minimum(w["steps"], args.steps_cap)
     return w
 
 
@@ -134,10 +147,11 @@ def run_ours(args, rank, world, device):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
     if args.workload in ("sweep", "plain"):
-        w = sweep_workload(rank) if args.workload == "sweep" else plain_workload(rank)
+        w = sweep_workload(rank, args) if args.workload == "sweep" else plain_workload(rank)
         sched = sde.SDE_SCHED_PERSISTENT if args.workload == "sweep" else sde.SDE_SCHED_PLAIN
         ens = sde.Ensemble.josephson(w["points"], w["paths"], w["steps"], w["seed"],
-                                     steps_per_period=w["steps_per_period"], schedule=sched)
+                                     steps_per_period=w["steps_per_period"], schedule=sched,
+                                     block_threads=args.block, paths_per_thread=args.ilp)
         n = int(w["paths"].sum())
         units = float((w["paths"] * w["steps"]).sum())
         n_end = int(w["steps"].max())
@@ -163,7 +177,10 @@ def run_ours(args, rank, world, device):
         launches_per_step = (1 if sched == sde.SDE_SCHED_PERSISTENT else len(w["points"])) + 1
         metric = "path-steps/sec"
         flop_per_unit = PAPER_FLOP_PER_STEP
-        cfg = {"workload": "josephson_sweep_512pts" if args.workload == "sweep" else "josephson_plain_1024",
+        name = "josephson_sweep_%dpts" % len(w["points"]) if args.workload == "sweep" else "josephson_plain_1024"
+        if args.steps_cap:
+            name += "_cap%d" % args.steps_cap
+        cfg = {"workload": name,
                "points": len(w["points"]), "total_paths": n, "path_steps": units,
                "steps_per_period": w["steps_per_period"],
                "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
@@ -239,12 +256,12 @@ def run_ours(args, rank, world, device):
 
     # end to end through the public API with host buffers
     e2e_ms = []
-    for _ in range(max(2, min(args.steps, 5))):
+    for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         step_e2e()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = statistics.median(e2e_ms)
+    e2e = statistics.median(e2e_ms) if e2e_ms else float("nan")
 
     k_ms = statistics.mean(kernel_ms)
     achieved = flop_per_unit * units / (k_ms * 1e-3) / 1e12

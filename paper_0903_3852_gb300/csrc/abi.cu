@@ -158,11 +158,17 @@ int persistent_grid(const sde_ctx *c, int ilp, int block) {
 }
 
 // Enqueue the work of one Josephson run (no graph).
+// Events recorded while a stream is being captured must be external records
+// to become event nodes of the graph.
+cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp, int block,
-                      bool time_it) {
+                      bool time_it, bool capturing = false) {
   JJLaunchArgs a = jj_args(c, r, ilp);
   const JJUnitList &L = c->units[ilp];
-  if (time_it) SDE_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  if (time_it) SDE_CUDA_TRY(record(c->ev0, s, capturing));
   if (c->cfg.schedule == SDE_SCHED_PERSISTENT) {
     if (L.n_units > 0) {
       SDE_CUDA_TRY(cudaMemsetAsync(c->queue, 0, sizeof(uint32_t), s));
@@ -180,7 +186,7 @@ sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp
       SDE_CUDA_TRY(jj_launch(a, ilp, block, grid, s));
     }
   }
-  if (time_it) SDE_CUDA_TRY(cudaEventRecord(c->ev1, s));
+  if (time_it) SDE_CUDA_TRY(record(c->ev1, s, capturing));
   SDE_CUDA_TRY(jj_finalize(c->consts, L.point_range, c->n_points, c->partials, r->n_end, c->obs, s));
   return SDE_OK;
 }
@@ -356,7 +362,7 @@ sde_status run_graph(sde_ctx *c, const sde_run_desc *r, cudaStream_t s) {
     c->gvalid = false;
     cudaGraph_t g = nullptr;
     SDE_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    sde_status st = jj_enqueue(c, r, c->cap_stream, c->ilp, c->block, true);
+    sde_status st = jj_enqueue(c, r, c->cap_stream, c->ilp, c->block, true, true);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (st != SDE_OK) {
       if (g) cudaGraphDestroy(g);

@@ -17,8 +17,9 @@
 // FP32 resolution does not degrade as paths run away.
 //
 // The window average of v (the time-averaged velocity <<v>> of Sec. 5) is
-// summed in FP32 over blocks of 64 steps and flushed into an FP64 per-path
-// accumulator; per-warp moments of the per-path averages are FP64.
+// summed in FP32 over blocks of 64 steps (aligned to absolute step indices)
+// and flushed into an FP64 per-path accumulator; per-warp moments of the
+// per-path averages are FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -62,7 +63,6 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
 #pragma unroll
   for (int i = 0; i < ILP; ++i) acc[i] = 0.0f;
   const int64_t g0 = n0 >> 2, g1 = (n1 - 1) >> 2;
-  int since_flush = 0;
   for (int64_t g = g0; g <= g1; ++g) {
     float z[ILP][4];
 #pragma unroll
@@ -90,8 +90,9 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
         }
       }
     }
-    if (ACC && ++since_flush == 16) {
-      since_flush = 0;
+    // Flush the FP32 partial sums at absolute 64-step boundaries, so that a
+    // run split at any multiple of 64 steps reproduces the unsplit sums.
+    if (ACC && ((g + 1) & 15) == 0) {
 #pragma unroll
       for (int i = 0; i < ILP; ++i) {
         vs[i] += (double)acc[i];
