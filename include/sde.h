@@ -215,6 +215,43 @@ sde_status sde_philox4x32_10(const uint32_t *ctr_dev, uint64_t seed, uint32_t *o
 sde_status sde_box_muller(const uint32_t *ctr_dev, uint64_t seed, float *z_dev, int64_t n,
                           void *stream);
 
+/*
+ * Allocation-free run of one Eq. 1 parameter point.  The paper has no
+ * counterpart: this is an interface for callers that must not allocate
+ * device memory -- code running inside another framework's memory pool or
+ * arena, which forbids allocations it does not manage; code invoked while a
+ * host program captures the stream into a CUDA graph, where cudaMalloc is
+ * not allowed; and hosts that reserve all device memory at start-up.
+ *
+ * It computes what sde_create + sde_run_ensemble + the observables would
+ * for a single point with the plain schedule (one thread per path, warps of
+ * 32 paths): same state layout and meaning as sde_run_desc, one
+ * sde_obs_row written to obs_dev (device).  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its only scratch, one reduction
+ * partial per 32 paths, is a fixed array of SDE_NOALLOC_MAX_PATHS / 32
+ * entries (768 KiB) in the library's static device memory, held by every
+ * GPU that loads the library until the process exits.
+ *
+ *  - n_paths above SDE_NOALLOC_MAX_PATHS returns SDE_ERR_INVALID_ARG.
+ *  - The first call on each device looks up that array's device address
+ *    (cudaGetSymbolAddress, with that device current); make the first call
+ *    on a device before any stream capture begins.
+ *  - All calls on a device share the array.  Calls that can overlap on the
+ *    GPU (different streams without ordering, or host threads) race on it
+ *    and must be serialised by the caller.  Each call writes every entry it
+ *    reads, so leftovers from earlier calls do no harm.
+ *  - Non-finite states are not latched; they appear in the outputs.
+ */
+#define SDE_NOALLOC_MAX_PATHS (1 << 20)
+
+sde_status sde_josephson_run_noalloc(const sde_jj_point *point_host, int32_t steps_per_period,
+                                     int64_t n_paths, int64_t total_steps, uint64_t seed,
+                                     int64_t n_begin, int64_t n_end, const float *x_in_dev,
+                                     const float *v_in_dev, const int32_t *w_in_dev,
+                                     const double *vsum_in_dev, float *x_out_dev, float *v_out_dev,
+                                     int32_t *w_out_dev, double *vsum_out_dev, sde_obs_row *obs_dev,
+                                     void *stream);
+
 /* Version of this ABI (major * 100 + minor). */
 int32_t sde_abi_version(void);
 

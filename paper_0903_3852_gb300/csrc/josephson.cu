@@ -23,6 +23,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <mutex>
+#include <string>
+
 #include "internal.h"
 #include "philox.cuh"
 
@@ -355,4 +358,202 @@ cudaError_t box_muller_fill(const uint32_t *ctr, uint64_t seed, float *z, int64_
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the per-path kernel (sde_josephson_run_noalloc).
+//
+// Some callers cannot call cudaMalloc: code that runs inside another
+// framework's memory pool or arena (which forbids allocations behind its
+// back), code that is itself being captured into a CUDA graph by a host
+// program, or embedded/real-time hosts that pre-reserve all device memory at
+// start-up.  For them this entry point keeps its only scratch -- one
+// reduction partial per warp of 32 paths -- in a fixed array in the
+// library's static device memory instead of a workspace allocated by
+// sde_create.  Every GPU that loads the library holds this array until the
+// process exits.
+// ---------------------------------------------------------------------------
+
+#define SDE_NOALLOC_UNITS (SDE_NOALLOC_MAX_PATHS / 32)
+
+namespace {
+
+// 32768 partials x 24 bytes = 768 KiB.  Shared by every call on a device;
+// it keeps the previous call's contents.  Each call writes every slot it
+// later reads, so nothing has to be cleared first.
+static __device__ __align__(256) Moments g_noalloc_partials[SDE_NOALLOC_UNITS];
+
+struct NoallocArgs {
+  sde_jj_point p;
+  int32_t P;
+  int32_t n_paths;
+  int64_t steps;
+  int64_t n_begin, n_end;
+  uint64_t seed;
+  JJState st;
+  Moments *partials;  // device address of g_noalloc_partials
+};
+
+// One warp per 32 paths, one path per thread: the same arithmetic and the same
+// unit decomposition as the plain schedule with one path per thread.
+__global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
+  extern __shared__ float drive_s[];
+  const double dt = 2.0 * 3.14159265358979323846 / (A.p.omega * (double)A.P);
+  for (int i = threadIdx.x; i < A.P; i += blockDim.x)
+    drive_s[i] = (float)cospi(2.0 * (double)i / (double)A.P);
+  __syncthreads();
+  JJConsts c;
+  c.gamma = (float)A.p.gamma;
+  c.a = (float)A.p.a;
+  c.f = (float)A.p.f;
+  c.dt = (float)dt;
+  c.h = (float)(0.5 * dt);
+  c.s = (float)sqrt(2.0 * A.p.gamma * A.p.D * dt);
+  c.paths = A.n_paths;
+  c.pad = 0;
+  c.steps = A.steps;
+  c.wstart = A.steps - A.steps / 2;
+  c.path_offset = 0;
+  c.dt64 = dt;
+  const int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int n_units = (A.n_paths + 31) / 32;
+  if (u >= n_units) return;
+  const int lane = threadIdx.x & 31;
+  const uint2 key = seed_to_key(A.seed);
+  const int j = u * 32 + lane;
+  const bool valid = j < A.n_paths;
+  float x[1] = {0.0f}, v[1] = {0.0f};
+  int w[1] = {0};
+  double vs[1] = {0.0};
+  const uint32_t pid[1] = {(uint32_t)j};
+  if (valid) {
+    x[0] = A.st.x_in[j];
+    v[0] = A.st.v_in[j];
+    if (A.st.w_in) w[0] = A.st.w_in[j];
+    if (A.st.vsum_in) vs[0] = A.st.vsum_in[j];
+  }
+  const float fl = floorf(x[0]);
+  x[0] -= fl;
+  w[0] += (int)fl;
+  const int64_t ne = A.n_end < c.steps ? A.n_end : c.steps;
+  if (A.n_begin < ne) {
+    int k = (int)(A.n_begin % A.P);
+    const int64_t split = ne < c.wstart ? ne : c.wstart;
+    jj_segment<1, false>(x, w, v, vs, c, drive_s, A.P, k, A.n_begin, split, key, pid, 0u);
+    jj_segment<1, true>(x, w, v, vs, c, drive_s, A.P, k, A.n_begin > c.wstart ? A.n_begin : c.wstart, ne,
+                        key, pid, 0u);
+  }
+  if (valid) {
+    A.st.x_out[j] = x[0];
+    A.st.v_out[j] = v[0];
+    A.st.w_out[j] = w[0];
+    A.st.vsum_out[j] = vs[0];
+  }
+  const int64_t wcount = ne > c.wstart ? ne - c.wstart : 0;
+  const double m = (valid && wcount > 0) ? vs[0] / (double)wcount : 0.0;
+  const double cnt = warp_sum((valid && wcount > 0) ? 1.0 : 0.0);
+  const double mean = cnt > 0.0 ? warp_sum(m) / cnt : 0.0;
+  const double d = (valid && wcount > 0) ? m - mean : 0.0;
+  const double m2 = warp_sum(d * d);
+  if (lane == 0) A.partials[u] = Moments{cnt, mean, m2};
+}
+
+__global__ void jj_noalloc_finalize(const Moments *partials, int n_units, int64_t steps, double dt,
+                                    int64_t n_end, sde_obs_row *obs) {
+  const int lane = threadIdx.x & 31;
+  Moments m{0.0, 0.0, 0.0};
+  for (int u = lane; u < n_units; u += 32) m = merge(m, partials[u]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Moments q;
+    q.n = __shfl_down_sync(0xffffffffu, m.n, o);
+    q.mean = __shfl_down_sync(0xffffffffu, m.mean, o);
+    q.m2 = __shfl_down_sync(0xffffffffu, m.m2, o);
+    if (lane + o < 32) m = merge(m, q);
+  }
+  if (lane == 0) {
+    const int64_t reach = n_end < steps ? n_end : steps;
+    sde_obs_row row;
+    row.count = m.n;
+    row.mean = m.n > 0.0 ? m.mean : 0.0;
+    row.var = m.n > 1.0 ? m.m2 / (m.n - 1.0) : 0.0;
+    row.se = m.n > 0.0 ? sqrt(row.var / m.n) : 0.0;
+    row.t = (double)reach * dt;
+    *obs = row;
+  }
+}
+
+}  // namespace
+
+namespace {
+// Device address of g_noalloc_partials, resolved once per device.
+constexpr int kMaxDevices = 64;
+Moments *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
 }  // namespace sde
+
+extern "C" sde_status sde_josephson_run_noalloc(const sde_jj_point *point, int32_t steps_per_period,
+                                                int64_t n_paths, int64_t total_steps, uint64_t seed,
+                                                int64_t n_begin, int64_t n_end, const float *x_in_dev,
+                                                const float *v_in_dev, const int32_t *w_in_dev,
+                                                const double *vsum_in_dev, float *x_out_dev,
+                                                float *v_out_dev, int32_t *w_out_dev,
+                                                double *vsum_out_dev, sde_obs_row *obs_dev,
+                                                void *stream) {
+  using namespace sde;
+  clear_error();
+  SDE_CHECK_ARG(point != nullptr, "point is NULL");
+  SDE_CHECK_ARG(n_paths >= 0, "n_paths must be >= 0");
+  if (n_paths > SDE_NOALLOC_MAX_PATHS) {
+    set_error("invalid argument: sde_josephson_run_noalloc handles at most " +
+              std::to_string(SDE_NOALLOC_MAX_PATHS) + " paths per call (got " +
+              std::to_string(n_paths) + "); use sde_create/sde_run_ensemble for larger ensembles");
+    return SDE_ERR_INVALID_ARG;
+  }
+  SDE_CHECK_ARG(steps_per_period >= 1 && steps_per_period <= 4096, "steps_per_period must be in [1, 4096]");
+  SDE_CHECK_ARG(total_steps >= 0 && total_steps <= (1ll << 33), "total_steps out of range");
+  SDE_CHECK_ARG(n_begin >= 0 && n_end >= n_begin && n_end <= (1ll << 33), "need 0 <= n_begin <= n_end");
+  SDE_CHECK_ARG(isfinite(point->gamma) && isfinite(point->a) && isfinite(point->omega) &&
+                    isfinite(point->f) && isfinite(point->D),
+                "point parameters must be finite");
+  SDE_CHECK_ARG(point->omega > 0.0 && point->gamma > 0.0 && point->D >= 0.0,
+                "need omega > 0, gamma > 0, D >= 0");
+  SDE_CHECK_ARG(obs_dev != nullptr, "obs_dev is NULL");
+  if (n_paths > 0)
+    SDE_CHECK_ARG(x_in_dev && v_in_dev && x_out_dev && v_out_dev && w_out_dev && vsum_out_dev,
+                  "x_in, v_in, x_out, v_out, w_out and vsum_out must be non-NULL");
+  int dev = 0;
+  SDE_CUDA_TRY(cudaGetDevice(&dev));
+  SDE_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "device index out of range");
+  Moments *partials = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_partials)");
+      g_noalloc_ptr[dev] = (Moments *)p;
+    }
+    partials = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  NoallocArgs a{};
+  a.p = *point;
+  a.P = steps_per_period;
+  a.n_paths = (int32_t)n_paths;
+  a.steps = total_steps;
+  a.n_begin = n_begin;
+  a.n_end = n_end;
+  a.seed = seed;
+  a.st = JJState{x_in_dev, v_in_dev, w_in_dev, vsum_in_dev, x_out_dev, v_out_dev, w_out_dev, vsum_out_dev};
+  a.partials = partials;
+  const int n_units = (int)((n_paths + 31) / 32);
+  if (n_units > 0) {
+    jj_noalloc_kernel<<<(n_units + 7) / 8, 256, sizeof(float) * steps_per_period, s>>>(a);
+    SDE_CUDA_TRY(cudaGetLastError());
+  }
+  const double dt = 2.0 * 3.14159265358979323846 / (point->omega * (double)steps_per_period);
+  jj_noalloc_finalize<<<1, 32, 0, s>>>(partials, n_units, total_steps, dt, n_end, obs_dev);
+  SDE_CUDA_TRY(cudaGetLastError());
+  return SDE_OK;
+}

@@ -83,7 +83,12 @@ SIGNATURES = [
     ("sde_philox4x32_10", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_box_muller", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_abi_version", ctypes.c_int32, []),
+    ("sde_josephson_run_noalloc", ctypes.c_int,
+     [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+      ctypes.c_int64, ctypes.c_int64] + [_VP] * 9 + [_VP]),
 ]
+
+NOALLOC_MAX_PATHS = 1 << 20
 
 
 def lib():
@@ -248,3 +253,17 @@ class Ensemble:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def josephson_run_noalloc(point, steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
+                          x_in, v_in, x_out, v_out, w_out, vsum_out, obs_out, w_in=None, vsum_in=None,
+                          stream=None):
+    """sde_josephson_run_noalloc: one parameter point, no device allocation by the
+    library (scratch lives in a fixed static array of NOALLOC_MAX_PATHS / 32
+    partials).  obs_out: a CUDA tensor of 5 float64 (one sde_obs_row)."""
+    p = JJPoint(point["gamma"], point["a"], point["omega"], point["f"], point["D"])
+    assert obs_out.numel() * obs_out.element_size() >= ctypes.sizeof(ObsRow)
+    _check(lib().sde_josephson_run_noalloc(
+        ctypes.byref(p), steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
+        _ptr(x_in), _ptr(v_in), _ptr(w_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(w_out),
+        _ptr(vsum_out), _ptr(obs_out), _stream(stream)))
