@@ -199,6 +199,24 @@ sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads,
 sde_status sde_last_kernel_ms(sde_ctx *ctx, float *ms);
 
 /*
+ * Load the coupling matrix of the general Kuramoto models (Eq. 2, K_ij):
+ * K_dev is N x N FP32, row-major, row i = the oscillator that receives
+ * sum_j K_ij sin(x_j - x_i).  SDE_KURAMOTO_GENERAL keeps a BF16 copy (the
+ * tensor-core operand), SDE_KURAMOTO_GENERAL_FP32 an FP32 copy; K_dev may be
+ * freed once the stream has passed this call.  Must precede sde_run_ensemble.
+ * Errors: SDE_ERR_INVALID_ARG (not a general model, NULL K).
+ */
+sde_status sde_set_coupling(sde_ctx *ctx, const float *K_dev, void *stream);
+
+/*
+ * Coupling sums of Eq. 2 for every replica through the context's coupling
+ * path: out_dev[r][i] = sum_j K_ij sin(phi_j - phi_i) (uniform models:
+ * K_ij = K/N; mean-field form of Eq. 3 evaluated pairwise; general models:
+ * the GEMM form, BF16 or FP32).  phi_dev, out_dev: [n_replicas][n_osc] FP32.
+ */
+sde_status sde_kuramoto_coupling(sde_ctx *ctx, const float *phi_dev, float *out_dev, void *stream);
+
+/*
  * Philox4x32-10 (Salmon et al., SC'11; replaces the xorshift generator of
  * Sec. 4.1): out_dev[4i..4i+3] = Philox(counter ctr_dev[4i..4i+3], key =
  * (seed low word, seed high word)).  n counters, n >= 0, device arrays.

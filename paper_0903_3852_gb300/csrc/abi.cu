@@ -520,6 +520,20 @@ sde_status sde_last_kernel_ms(sde_ctx *c, float *ms) {
   return SDE_OK;
 }
 
+sde_status sde_set_coupling(sde_ctx *c, const float *K_dev, void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
+  SDE_CHECK_ARG(c->kur != nullptr, "sde_set_coupling applies to Kuramoto contexts");
+  return kuramoto_set_coupling(c->kur, K_dev, (cudaStream_t)stream);
+}
+
+sde_status sde_kuramoto_coupling(sde_ctx *c, const float *phi_dev, float *out_dev, void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
+  SDE_CHECK_ARG(c->kur != nullptr, "sde_kuramoto_coupling applies to Kuramoto contexts");
+  return kuramoto_coupling(c->kur, phi_dev, out_dev, (cudaStream_t)stream);
+}
+
 sde_status sde_philox4x32_10(const uint32_t *ctr, uint64_t seed, uint32_t *out, int64_t n,
                              void *stream) {
   clear_error();

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPair
     const int64_t gi = base + idx[k];
     float z[4];
     gauss4((uint32_t)(n >> 2), (uint32_t)idx[k], (uint32_t)rep, kTagKuramoto, key, z);
-    const float psi = z[n & 3];
+    const float psi = pick4(z, (int)(n & 3));
     const float wdt = A.omega[gi] * A.wscale;
     if (STAGE == 0) {
       const float d1 = fmaf(A.sc, psi, fmaf(A.kc, acc[k], wdt));
@@ -300,6 +300,30 @@ __global__ void kur_obs_kernel(const double *r, int64_t rows, int64_t R, int64_t
     o.t = (double)n * dt;
     obs[row] = o;
   }
+}
+
+// Direct coupling sums for the uniform models: out[r][i] = (K/N) sum_j
+// sin(x_j - x_i), accurate sinpif per pair (inspection path, not the
+// integrator).
+__global__ void kur_coupling_uniform_kernel(const uint32_t *theta, float *out, int64_t N, float KoverN) {
+  __shared__ float src_s[256];
+  const int rep = blockIdx.y;
+  const int64_t base = (int64_t)rep * N;
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const float ti = i < N ? (float)(int32_t)theta[base + i] * 2.3283064365386963e-10f : 0.0f;
+  float acc = 0.0f;
+  for (int64_t j0 = 0; j0 < N; j0 += 256) {
+    const int cnt = (N - j0) < 256 ? (int)(N - j0) : 256;
+    if (threadIdx.x < cnt) src_s[threadIdx.x] = (float)(int32_t)theta[base + j0 + threadIdx.x] * 2.3283064365386963e-10f;
+    __syncthreads();
+    for (int jj = 0; jj < cnt; ++jj) {
+      float d = src_s[jj] - ti;
+      d -= rintf(d);
+      acc += sinpif(2.0f * d);
+    }
+    __syncthreads();
+  }
+  if (i < N) out[base + i] = KoverN * acc;
 }
 
 template <int OPT>
@@ -503,6 +527,20 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
     SDE_CUDA_TRY(cudaGetLastError());
   }
   *rows = n_rows;
+  return SDE_OK;
+}
+
+sde_status kuramoto_coupling(KuramotoCtx *k, const float *phi_dev, float *out_dev, cudaStream_t s) {
+  SDE_CHECK_ARG(phi_dev != nullptr && out_dev != nullptr, "phi and out must be non-NULL");
+  const int64_t NR = k->N * k->R;
+  const int cvt_grid = (int)std::min<int64_t>((NR + 255) / 256, 4096);
+  kur_to_fixed<<<cvt_grid, 256, 0, s>>>(phi_dev, k->theta, NR);
+  SDE_CUDA_TRY(cudaGetLastError());
+  if (k->model == SDE_KURAMOTO_GENERAL || k->model == SDE_KURAMOTO_GENERAL_FP32)
+    return kuramoto_general_coupling(k, out_dev, s);
+  const dim3 grid((unsigned)((k->N + 255) / 256), (unsigned)k->R);
+  kur_coupling_uniform_kernel<<<grid, 256, 0, s>>>(k->theta, out_dev, k->N, (float)(k->K / (double)k->N));
+  SDE_CUDA_TRY(cudaGetLastError());
   return SDE_OK;
 }
 

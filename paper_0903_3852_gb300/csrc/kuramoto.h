@@ -18,6 +18,8 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
                         cudaEvent_t ev1, sde_obs_row *obs_in, sde_obs_row **obs,
                         int64_t *max_rows, int64_t *rows);
 sde_status kuramoto_set_coupling(KuramotoCtx *k, const float *K_dev, cudaStream_t s);
+// out[r][i] = sum_j K_ij sin(phi_j - phi_i) through the model's coupling path.
+sde_status kuramoto_coupling(KuramotoCtx *k, const float *phi_dev, float *out_dev, cudaStream_t s);
 void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread);
 void kuramoto_destroy(KuramotoCtx *k);
 

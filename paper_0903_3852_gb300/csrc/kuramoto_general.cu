@@ -1,18 +1,408 @@
 // kuramoto_general.cu -- Eq. 2 with a general coupling matrix K_ij.
+//
+// The coupling sum is rewritten with sin(x_j - x_i) = sin x_j cos x_i -
+// cos x_j sin x_i (the identity behind Eq. 3, applied row by row):
+//
+//   sum_j K_ij sin(x_j - x_i) = cos x_i P_s[i] - sin x_i P_c[i],
+//   P_s = K sin(x),  P_c = K cos(x),
+//
+// so one SRK2 stage of all R replicas is one GEMM of K (N x N) with the
+// 2R columns [sin x_r | cos x_r] plus an elementwise sub-step.  Two forms:
+//   SDE_KURAMOTO_GENERAL      BF16 operands on tcgen05, FP32 accumulation in
+//                             tensor memory (tc_gemm.cuh)
+//   SDE_KURAMOTO_GENERAL_FP32 FP32 operands, FP32 CUDA-core GEMM (the
+//                             baseline the tensor-core form is set against)
+// Phases are 32-bit fixed-point turns as in kuramoto.cu; the receiving
+// oscillator's own sin/cos are always evaluated in FP32 from its phase.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+
 #include "kuramoto.h"
 #include "kuramoto_internal.h"
+#include "philox.cuh"
+#include "tc_gemm.cuh"
 
 namespace sde {
 
-sde_status kuramoto_general_alloc(KuramotoCtx *) { return SDE_OK; }
-void kuramoto_general_free(KuramotoCtx *) {}
-sde_status kuramoto_general_run(KuramotoCtx *, const sde_run_desc *, cudaStream_t, double *) {
-  set_error("general coupling is not built yet");
-  return SDE_ERR_UNSUPPORTED;
+namespace {
+
+constexpr float kTurn = 2.3283064365386963e-10f;  // 2^-32
+
+__device__ __forceinline__ float signed_turns(uint32_t th) { return (float)(int32_t)th * kTurn; }
+
+template <typename T>
+__device__ __forceinline__ T to_op(float v);
+template <>
+__device__ __forceinline__ float to_op<float>(float v) {
+  return v;
 }
-sde_status kuramoto_set_coupling(KuramotoCtx *, const float *, cudaStream_t) {
-  set_error("general coupling is not built yet");
-  return SDE_ERR_UNSUPPORTED;
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// Operand rows [2r] = sin, [2r+1] = cos of every phase.
+template <typename T>
+__global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N, int64_t R) {
+  const int64_t total = N * R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / N, i = idx - r * N;
+    float s, c;
+    sincospif(2.0f * signed_turns(theta[idx]), &s, &c);
+    op[(2 * r) * N + i] = to_op<T>(s);
+    op[(2 * r + 1) * N + i] = to_op<T>(c);
+  }
+}
+
+// One SRK2 stage for every (replica, oscillator) from the GEMM output Dt.
+// STAGE 0: predictor theta~ = theta + dt/(2 pi) (omega + g1) + sqrt(2 D dt)/(2 pi) psi
+// STAGE 1: corrector theta' = theta + dt/(2 pi) (omega + (g1 + g2) / 2) + ... psi
+template <int STAGE, typename T>
+__global__ void kg_stage_kernel(const float *__restrict__ Dt, uint32_t *theta, uint32_t *theta_t, float *g1,
+                                const float *__restrict__ omega, T *op_next, int64_t N, int64_t R, int64_t n,
+                                float wscale, float kc, float kh, float sc, uint64_t seed) {
+  const int64_t total = N * R;
+  const uint2 key = seed_to_key(seed);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / N, i = idx - r * N;
+    const uint32_t th_i = STAGE == 0 ? theta[idx] : theta_t[idx];
+    float s, c;
+    sincospif(2.0f * signed_turns(th_i), &s, &c);
+    const float g = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
+    float z[4];
+    gauss4((uint32_t)(n >> 2), (uint32_t)i, (uint32_t)r, kTagKuramoto, key, z);
+    const float psi = pick4(z, (int)(n & 3));
+    const float wdt = omega[idx] * wscale;
+    uint32_t out;
+    if (STAGE == 0) {
+      const float d1 = fmaf(sc, psi, fmaf(kc, g, wdt));
+      out = theta[idx] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+      theta_t[idx] = out;
+      g1[idx] = g;
+    } else {
+      const float d = fmaf(sc, psi, fmaf(kh, g1[idx] + g, wdt));
+      out = theta[idx] + (uint32_t)__float2int_rn(d * 4294967296.0f);
+      theta[idx] = out;
+    }
+    float so, co;
+    sincospif(2.0f * signed_turns(out), &so, &co);
+    op_next[(2 * r) * N + i] = to_op<T>(so);
+    op_next[(2 * r + 1) * N + i] = to_op<T>(co);
+  }
+}
+
+// Coupling sums alone: out[r][i] = cos x_i Dt[2r][i] - sin x_i Dt[2r+1][i].
+__global__ void kg_coupling_kernel(const float *__restrict__ Dt, const uint32_t *theta, float *out, int64_t N,
+                                   int64_t R) {
+  const int64_t total = N * R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / N, i = idx - r * N;
+    float s, c;
+    sincospif(2.0f * signed_turns(theta[idx]), &s, &c);
+    out[idx] = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
+  }
+}
+
+__global__ void kg_to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// ---- FP32 CUDA-core GEMM (baseline): Dt[c][i] = sum_j K[i][j] B[c][j] ----
+// 128 x 128 tile per block of 256 threads, 8 x 8 outputs per thread, K
+// slices of 8 staged (transposed) in shared memory, double buffered.
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
+
+__global__ void __launch_bounds__(256) sgemm_nt_kernel(const float *__restrict__ A, const float *__restrict__ B,
+                                                       float *__restrict__ Dt, int M, int Ncols, int Kdim) {
+  __shared__ float As[2][SG_BK][SG_BM];
+  __shared__ float Bs[2][SG_BK][SG_BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads
+  const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;
+  // loader mapping: 128 rows x 8 k = 256 float4: row = tid >> 1, k4 = (tid & 1) * 4
+  const int lr = tid >> 1, lk = (tid & 1) * 4;
+  const float *Ap = A + (size_t)(m0 + lr) * Kdim + lk;
+  const float *Bp = B + (size_t)(n0 + lr) * Kdim + lk;
+  const bool a_ok = (m0 + lr) < M, b_ok = (n0 + lr) < Ncols;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+  float4 ra = a_ok ? *(const float4 *)Ap : make_float4(0, 0, 0, 0);
+  float4 rb = b_ok ? *(const float4 *)Bp : make_float4(0, 0, 0, 0);
+  int buf = 0;
+  As[0][lk + 0][lr] = ra.x;
+  As[0][lk + 1][lr] = ra.y;
+  As[0][lk + 2][lr] = ra.z;
+  As[0][lk + 3][lr] = ra.w;
+  Bs[0][lk + 0][lr] = rb.x;
+  Bs[0][lk + 1][lr] = rb.y;
+  Bs[0][lk + 2][lr] = rb.z;
+  Bs[0][lk + 3][lr] = rb.w;
+  __syncthreads();
+  for (int k0 = 0; k0 < Kdim; k0 += SG_BK) {
+    const bool more = k0 + SG_BK < Kdim;
+    if (more) {
+      ra = a_ok ? *(const float4 *)(Ap + k0 + SG_BK) : make_float4(0, 0, 0, 0);
+      rb = b_ok ? *(const float4 *)(Bp + k0 + SG_BK) : make_float4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      float a[8], b[8];
+      const float4 a0 = *(const float4 *)&As[buf][kk][ty * 4];
+      const float4 a1 = *(const float4 *)&As[buf][kk][64 + ty * 4];
+      const float4 b0 = *(const float4 *)&Bs[buf][kk][tx * 4];
+      const float4 b1 = *(const float4 *)&Bs[buf][kk][64 + tx * 4];
+      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+      b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+    if (more) {
+      buf ^= 1;
+      As[buf][lk + 0][lr] = ra.x;
+      As[buf][lk + 1][lr] = ra.y;
+      As[buf][lk + 2][lr] = ra.z;
+      As[buf][lk + 3][lr] = ra.w;
+      Bs[buf][lk + 0][lr] = rb.x;
+      Bs[buf][lk + 1][lr] = rb.y;
+      Bs[buf][lk + 2][lr] = rb.z;
+      Bs[buf][lk + 3][lr] = rb.w;
+      __syncthreads();
+    }
+  }
+  // rows of this thread: m0 + {ty*4 .. ty*4+3, 64+ty*4 .. 64+ty*4+3}; columns likewise with tx
+#pragma unroll
+  for (int y = 0; y < 8; ++y) {
+    const int col = n0 + (y < 4 ? tx * 4 + y : 64 + tx * 4 + (y - 4));
+    if (col >= Ncols) continue;
+    float *dst = Dt + (size_t)col * M;
+    const int r0 = m0 + ty * 4, r1 = m0 + 64 + ty * 4;
+    if (r0 + 3 < M) *(float4 *)(dst + r0) = make_float4(acc[0][y], acc[1][y], acc[2][y], acc[3][y]);
+    if (r1 + 3 < M) *(float4 *)(dst + r1) = make_float4(acc[4][y], acc[5][y], acc[6][y], acc[7][y]);
+  }
+}
+
+int grid_for(int64_t n, int sm_count) {
+  const int64_t b = (n + 255) / 256;
+  return (int)std::min<int64_t>(b, (int64_t)sm_count * 16);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2D BF16 tensor map: rows x cols (cols contiguous), box of box_rows x 64.
+sde_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return SDE_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
+    return SDE_ERR_CUDA;
+  }
+  return SDE_OK;
+}
+
+struct GemmPlan {
+  CUtensorMap mapK;
+  CUtensorMap mapOp[2];
+  int bn = 0;
+};
+
+bool is_tc(const KuramotoCtx *k) { return k->model == SDE_KURAMOTO_GENERAL; }
+
+void *op_buf(KuramotoCtx *k, int which) {
+  if (is_tc(k)) return (void *)(k->Bt + (size_t)which * 2 * k->R * k->N);
+  return (void *)(k->Bt32 + (size_t)which * 2 * k->R * k->N);
+}
+
+cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s) {
+  const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
+  if (is_tc(k)) {
+    GemmPlan *g = (GemmPlan *)k->gemm_plan;
+    if (g->bn == 256) {
+      dim3 grid(M / tc::BM, Ncols / 256);
+      tc::tc_gemm_bf16_kernel<256><<<grid, tc::THREADS, tc::Shape<256>::SMEM_BYTES, s>>>(
+          g->mapK, g->mapOp[which], k->P, M, Kdim, k->err);
+    } else {
+      dim3 grid(M / tc::BM, Ncols / 128);
+      tc::tc_gemm_bf16_kernel<128><<<grid, tc::THREADS, tc::Shape<128>::SMEM_BYTES, s>>>(
+          g->mapK, g->mapOp[which], k->P, M, Kdim, k->err);
+    }
+  } else {
+    dim3 grid((M + SG_BM - 1) / SG_BM, (Ncols + SG_BN - 1) / SG_BN);
+    sgemm_nt_kernel<<<grid, 256, 0, s>>>(k->Kf32, (const float *)op_buf(k, which), k->P, M, Ncols, Kdim);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_operand(KuramotoCtx *k, int which, cudaStream_t s) {
+  const int grid = grid_for(k->N * k->R, k->sm_count);
+  if (is_tc(k))
+    kg_operand_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(k->theta, (__nv_bfloat16 *)op_buf(k, which), k->N, k->R);
+  else
+    kg_operand_kernel<float><<<grid, 256, 0, s>>>(k->theta, (float *)op_buf(k, which), k->N, k->R);
+  return cudaGetLastError();
+}
+
+template <int STAGE>
+cudaError_t launch_stage(KuramotoCtx *k, int next, const float *omega, int64_t n, cudaStream_t s) {
+  const double inv2pi = 0.15915494309189533577;
+  const float wscale = (float)(k->dt * inv2pi);
+  const float kc = (float)(k->dt * inv2pi);
+  const float kh = (float)(0.5 * k->dt * inv2pi);
+  const float sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
+  const int grid = grid_for(k->N * k->R, k->sm_count);
+  if (is_tc(k))
+    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid, 256, 0, s>>>(
+        k->P, k->theta, k->theta_t, k->g1, omega, (__nv_bfloat16 *)op_buf(k, next), k->N, k->R, n, wscale, kc, kh,
+        sc, k->seed);
+  else
+    kg_stage_kernel<STAGE, float><<<grid, 256, 0, s>>>(k->P, k->theta, k->theta_t, k->g1, omega,
+                                                       (float *)op_buf(k, next), k->N, k->R, n, wscale, kc, kh,
+                                                       sc, k->seed);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+sde_status kuramoto_general_alloc(KuramotoCtx *k) {
+  const size_t NR = (size_t)k->N * (size_t)k->R;
+  const size_t NN = (size_t)k->N * (size_t)k->N;
+  if (is_tc(k)) {
+    if (k->N % tc::BM != 0 || (2 * k->R) % 128 != 0) {
+      set_error("invalid argument: the tensor-core form needs n_osc % 128 == 0 and n_replicas % 64 == 0 "
+                "(use SDE_KURAMOTO_GENERAL_FP32 for other sizes)");
+      return SDE_ERR_INVALID_ARG;
+    }
+  }
+  if (!is_tc(k) && k->N % 8 != 0) {
+    set_error("invalid argument: the FP32 general-coupling form needs n_osc % 8 == 0");
+    return SDE_ERR_INVALID_ARG;
+  }
+  cudaError_t e;
+  if ((e = cudaMalloc((void **)&k->theta_t, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void **)&k->g1, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void **)&k->P, NR * 2 * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if (is_tc(k)) {
+    if ((e = cudaMalloc((void **)&k->Kbf16, NN * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc((void **)&k->Bt, NR * 2 * 2 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    GemmPlan *g = new GemmPlan();
+    k->gemm_plan = g;
+    g->bn = (2 * k->R) % 256 == 0 ? 256 : 128;
+    sde_status st = make_map(&g->mapK, k->Kbf16, k->N, k->N, tc::BM);
+    if (st != SDE_OK) return st;
+    for (int w = 0; w < 2; ++w) {
+      st = make_map(&g->mapOp[w], op_buf(k, w), 2 * k->R, k->N, g->bn);
+      if (st != SDE_OK) return st;
+    }
+    if ((e = cudaFuncSetAttribute(tc::tc_gemm_bf16_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Shape<256>::SMEM_BYTES)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    if ((e = cudaFuncSetAttribute(tc::tc_gemm_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::Shape<128>::SMEM_BYTES)) != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute");
+  } else {
+    if ((e = cudaMalloc((void **)&k->Kf32, NN * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMalloc((void **)&k->Bt32, NR * 2 * 4 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  }
+  k->block = is_tc(k) ? tc::THREADS : 256;
+  k->opt = is_tc(k) ? ((GemmPlan *)k->gemm_plan)->bn : SG_BN;
+  return SDE_OK;
+}
+
+void kuramoto_general_free(KuramotoCtx *k) {
+  cudaFree(k->Kf32);
+  cudaFree(k->Kbf16);
+  cudaFree(k->Bt);
+  cudaFree(k->Bt32);
+  cudaFree(k->P);
+  delete (GemmPlan *)k->gemm_plan;
+  k->gemm_plan = nullptr;
+}
+
+sde_status kuramoto_set_coupling(KuramotoCtx *k, const float *K_dev, cudaStream_t s) {
+  if (!(k->model == SDE_KURAMOTO_GENERAL || k->model == SDE_KURAMOTO_GENERAL_FP32)) {
+    set_error("invalid argument: sde_set_coupling applies to the general-coupling models only");
+    return SDE_ERR_INVALID_ARG;
+  }
+  SDE_CHECK_ARG(K_dev != nullptr, "K is NULL");
+  const int64_t NN = k->N * k->N;
+  if (is_tc(k)) {
+    kg_to_bf16_kernel<<<grid_for(NN, k->sm_count), 256, 0, s>>>(K_dev, k->Kbf16, NN);
+    SDE_CUDA_TRY(cudaGetLastError());
+  } else {
+    SDE_CUDA_TRY(cudaMemcpyAsync(k->Kf32, K_dev, sizeof(float) * NN, cudaMemcpyDeviceToDevice, s));
+  }
+  k->have_K = true;
+  return SDE_OK;
+}
+
+sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, double *rbuf) {
+  if (!k->have_K) {
+    set_error("invalid argument: set the coupling matrix with sde_set_coupling before running");
+    return SDE_ERR_INVALID_ARG;
+  }
+  SDE_CUDA_TRY(launch_operand(k, 0, s));
+  int64_t sample = 0;
+  for (int64_t n = r->n_begin; n < r->n_end; ++n) {
+    if (k->M > 0 && (n - r->n_begin) % k->M == 0) {
+      SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
+      ++sample;
+    }
+    SDE_CUDA_TRY(launch_gemm(k, 0, s));
+    SDE_CUDA_TRY(launch_stage<0>(k, 1, r->omega_dev, n, s));
+    SDE_CUDA_TRY(launch_gemm(k, 1, s));
+    SDE_CUDA_TRY(launch_stage<1>(k, 0, r->omega_dev, n, s));
+  }
+  if (k->M > 0) SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
+  return SDE_OK;
+}
+
+sde_status kuramoto_general_coupling(KuramotoCtx *k, float *out, cudaStream_t s) {
+  if (!k->have_K) {
+    set_error("invalid argument: set the coupling matrix with sde_set_coupling first");
+    return SDE_ERR_INVALID_ARG;
+  }
+  SDE_CUDA_TRY(launch_operand(k, 0, s));
+  SDE_CUDA_TRY(launch_gemm(k, 0, s));
+  kg_coupling_kernel<<<grid_for(k->N * k->R, k->sm_count), 256, 0, s>>>(k->P, k->theta, out, k->N, k->R);
+  SDE_CUDA_TRY(cudaGetLastError());
+  return SDE_OK;
 }
 
 }  // namespace sde

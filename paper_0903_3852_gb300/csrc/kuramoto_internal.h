@@ -70,5 +70,6 @@ cudaError_t kur_order_launch(const uint32_t *theta, int64_t N, int64_t R, double
 sde_status kuramoto_general_alloc(KuramotoCtx *k);
 void kuramoto_general_free(KuramotoCtx *k);
 sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, double *rbuf);
+sde_status kuramoto_general_coupling(KuramotoCtx *k, float *out, cudaStream_t s);
 
 }  // namespace sde

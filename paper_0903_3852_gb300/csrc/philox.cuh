@@ -58,4 +58,9 @@ __device__ __forceinline__ void gauss4(uint32_t g, uint32_t c1, uint32_t c2, uin
   box_muller(r.z, r.w, z[2], z[3]);
 }
 
+// Element k (0..3) of a 4-vector without dynamic register indexing.
+__device__ __forceinline__ float pick4(const float (&z)[4], int k) {
+  return k == 0 ? z[0] : (k == 1 ? z[1] : (k == 2 ? z[2] : z[3]));
+}
+
 }  // namespace sde

@@ -1,0 +1,271 @@
+// tc_gemm.cuh -- BF16 GEMM on the 5th-generation tensor cores (tcgen05) for
+// the general Kuramoto coupling of Eq. 2:
+//
+//   Dt[c][i] = sum_j K[i][j] * Bt[c][j],   Bt rows c = 2r (sin phi_r), 2r+1 (cos phi_r)
+//
+// so that sum_j K_ij sin(phi_j - phi_i) = cos(phi_i) Dt[2r][i] - sin(phi_i) Dt[2r+1][i].
+// A = K (N x N, row i contiguous in j) and B = Bt (2R x N, row c contiguous in
+// j) are both K-major; one CTA computes a 128 x BN tile of D with FP32
+// accumulators in tensor memory:
+//   warp 0, one thread : TMA producer (cp.async.bulk.tensor, 128B swizzle),
+//                        STAGES-deep ring of (A, B) tiles guarded by mbarriers
+//   warp 1, one thread : tcgen05.mma issuer (M = 128, N = BN, K = 16 per MMA),
+//                        tcgen05.commit frees a ring slot / signals the end
+//   all 8 warps        : epilogue, tcgen05.ld 32x32b of their TMEM lane
+//                        quarter, stores of Dt (each warp store is one 128 B
+//                        row segment: the TMEM lane is the row index i)
+// Every mbarrier wait is bounded (about one second of %globaltimer); on expiry
+// the CTA records SDE kErrTimeout, drains its own TMA loads and MMAs with
+// bounded waits, frees its tensor memory and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sde {
+namespace tc {
+
+constexpr int BM = 128;  // rows of D per CTA (MMA M)
+constexpr int BK = 64;   // K elements per ring slot: one 128-byte swizzle row
+constexpr int UMMA_K = 16;
+constexpr int STAGES = 4;
+constexpr int THREADS = 256;
+constexpr uint64_t kTimeoutNs = 1000000000ull;
+
+template <int BN>
+struct Shape {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+  static constexpr int TMEM_COLS = BN;                            // FP32 accumulator columns
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
+// Wait for the phase of `parity` to complete; false if the CTA's abort flag
+// is raised or about a second passes (then the flag is raised).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of tcgen05 for a K-major tile written by
+// TMA with 128-byte swizzling: rows of 128 bytes, 8-row groups 1024 bytes
+// apart (stride byte offset), descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p) {
+  const uint64_t addr = smem_addr(p);
+  uint64_t d = (addr >> 4) & 0x3FFFull;
+  d |= 1ull << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= 1ull << 46;                  // version
+  d |= 2ull << 61;                  // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// D = A * B^T over K = Kdim; Dt is written transposed ([col][row], rows
+// contiguous) so that each column of the tile is one coalesced run.
+// Requires M % 128 == 0, Ncols % BN == 0, Kdim % 64 == 0 (checked by the host).
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                        float *__restrict__ Dt, int M, int Kdim, uint32_t *err) {
+  using S = Shape<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *smA = smem;
+  uint8_t *smB = smem + STAGES * S::A_BYTES;
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = Kdim / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"((uint32_t)S::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
+      mbar_arrive_expect_tx(&full_bar[s], (uint32_t)S::STAGE_BYTES);
+      tma_load_2d(smA + s * S::A_BYTES, &mapA, &full_bar[s], kb * BK, m0);
+      tma_load_2d(smB + s * S::B_BYTES, &mapB, &full_bar[s], kb * BK, n0);
+      issued = kb + 1;
+    }
+    if (abort_flag) {
+      // drain this CTA's own loads still in flight (bounded)
+      volatile int no_abort = 0;
+      for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+        mbar_wait(&full_bar[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, &no_abort);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+      tmem_fence_after();
+      const uint64_t adesc = smem_desc_sw128(smA + s * S::A_BYTES);
+      const uint64_t bdesc = smem_desc_sw128(smB + s * S::B_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / UMMA_K; ++k)
+        umma_bf16(tmem, adesc + (uint64_t)(k * UMMA_K * 2 / 16), bdesc + (uint64_t)(k * UMMA_K * 2 / 16),
+                  idesc, (kb | k) != 0 ? 1u : 0u);
+      umma_commit(&empty_bar[s]);
+    }
+    umma_commit(&acc_bar);  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---- epilogue: all warps ----
+  volatile int no_abort = 0;
+  const bool ok = mbar_wait(&acc_bar, 0, &no_abort) && !abort_flag;
+  tmem_fence_after();
+  if (ok) {
+    const int q = warp & 3;      // TMEM lane quarter this warp may access
+    const int half = warp >> 2;  // which half of the BN columns
+    const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 2; cc += 32) {
+      const int col = half * (BN / 2) + cc;
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Dt[(size_t)(n0 + col + i) * (size_t)M + row] = v[i];
+    }
+  }
+  tmem_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)S::TMEM_COLS)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && (abort_flag || !ok)) atomicOr(err, kErrTimeout);
+}
+
+}  // namespace tc
+}  // namespace sde

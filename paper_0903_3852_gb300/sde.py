@@ -83,6 +83,8 @@ SIGNATURES = [
     ("sde_philox4x32_10", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_box_muller", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_abi_version", ctypes.c_int32, []),
+    ("sde_set_coupling", ctypes.c_int, [_VP, _VP, _VP]),
+    ("sde_kuramoto_coupling", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("sde_josephson_run_noalloc", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_int64, ctypes.c_int64] + [_VP] * 9 + [_VP]),
@@ -214,6 +216,17 @@ class Ensemble:
         r.phi_in_dev, r.phi_out_dev, r.omega_dev = _ptr(phi_in), _ptr(phi_out), _ptr(omega)
         r.r_out_dev = _ptr(r_out)
         _check(lib().sde_run_ensemble(self._h, ctypes.byref(r), _stream(stream)))
+
+    def set_coupling(self, K, stream=None):
+        """K: (N, N) float32 CUDA tensor, row i = receiving oscillator."""
+        _check(lib().sde_set_coupling(self._h, _ptr(K), _stream(stream)))
+
+    def coupling(self, phi, stream=None):
+        """Coupling sums sum_j K_ij sin(phi_j - phi_i) for phi of shape (R, N)."""
+        import torch
+        out = torch.empty_like(phi)
+        _check(lib().sde_kuramoto_coupling(self._h, _ptr(phi), _ptr(out), _stream(stream)))
+        return out
 
     def observables(self, capacity=None):
         """Synchronise and return the FP64 observables as a structured numpy array
