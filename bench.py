@@ -42,10 +42,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
-                    choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise"])
+                    choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise",
+                             "kuramoto-general", "kuramoto-general-fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairwise-steps", type=int, default=200,
                     help="steps per bench step of the pairwise Kuramoto workload")
+    ap.add_argument("--general-steps", type=int, default=0,
+                    help="steps per bench step of the general-coupling workloads "
+                         "(default: all 5000 for BF16, 100 for the FP32 baseline)")
     # reduced cases for profiler captures (not bench lines)
     ap.add_argument("--points", type=int, default=0, help="sweep: keep only the first N points")
     ap.add_argument("--steps-cap", type=int, default=0, help="sweep: cap every point's step count")
@@ -130,6 +134,14 @@ def plain_workload(rank):
     return w
 
 
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "of measured (MEASURED_PEAKS.json)"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
 def fp32_peak_tflops(props):
     # 128 FP32 lanes per SM on Blackwell, one FMA (2 FLOP) per lane per clock,
     # at the maximum SM clock of 2070 MHz.
@@ -175,6 +187,7 @@ def run_ours(args, rank, world, device):
         h2d = x_h.numel() * 4 + v_h.numel() * 4
         d2h = 40 * len(w["points"])
         launches_per_step = (1 if sched == sde.SDE_SCHED_PERSISTENT else len(w["points"])) + 1
+        launches_kernel = 1  # the timed region brackets the per-step launches as one
         metric = "path-steps/sec"
         flop_per_unit = PAPER_FLOP_PER_STEP
         name = "josephson_sweep_%dpts" % len(w["points"]) if args.workload == "sweep" else "josephson_plain_1024"
@@ -186,12 +199,12 @@ def run_ours(args, rank, world, device):
                "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
                "tuning": dict(zip(("block_threads", "paths_per_thread"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write); state 9 MB, compute-bound"}
-    else:
+    elif args.workload in ("kuramoto-meanfield", "kuramoto-pairwise"):
         w = inputs.kuramoto_uniform(seed=rank)
         model = sde.SDE_KURAMOTO_MEANFIELD if args.workload == "kuramoto-meanfield" else sde.SDE_KURAMOTO_PAIRWISE
         S = w["steps"] if model == sde.SDE_KURAMOTO_MEANFIELD else args.pairwise_steps
         ens = sde.Ensemble.kuramoto(model, w["n_osc"], w["replicas"], w["K"], w["D"], w["dt"], w["seed"],
-                                    sample_every=w["sample_every"])
+                                    sample_every=w["sample_every"], flags=sde.SDE_FLAG_TIME_KERNELS)
         phi_h = torch.from_numpy(w["phi0"]).pin_memory()
         phi_in = phi_h.to(device)
         om = torch.from_numpy(w["omega"]).to(device)
@@ -212,14 +225,51 @@ def run_ours(args, rank, world, device):
             metric = "oscillator-steps/sec"
             flop_per_unit = 66  # Appendix: 66 FLOP per step of the mean-field program
             launches_per_step = 4
+            flop_per_launch = flop_per_unit * units
         else:
             units = float(w["n_osc"] ** 2 * w["replicas"] * S)
             metric = "pair-terms/sec"
             flop_per_unit = 6  # Appendix: 44 + 6N FLOP per oscillator-step, 6 per pair term
             launches_per_step = 2 * S + S // w["sample_every"] + 4
+            flop_per_launch = flop_per_unit * w["n_osc"] ** 2 * w["replicas"]  # one stage launch
         cfg = {"workload": "kuramoto_%s_N%d_R%d" % (args.workload.split("-")[1], w["n_osc"], w["replicas"]),
                "steps_per_bench_step": S, "K": w["K"], "D": w["D"], "dt": w["dt"],
                "l2": "flushed between steps (256 MiB write)"}
+    else:
+        w = inputs.kuramoto_general(seed=rank)
+        tc = args.workload == "kuramoto-general"
+        model = sde.SDE_KURAMOTO_GENERAL if tc else sde.SDE_KURAMOTO_GENERAL_FP32
+        S = args.general_steps or (w["steps"] if tc else 100)
+        N, R = w["n_osc"], w["replicas"]
+        ens = sde.Ensemble.kuramoto(model, N, R, 0.0, w["D"], w["dt"], w["seed"],
+                                    sample_every=w["sample_every"], flags=sde.SDE_FLAG_TIME_KERNELS)
+        Kdev = torch.from_numpy(w["Kmat"]).to(device)
+        ens.set_coupling(Kdev)
+        del Kdev
+        phi_h = torch.from_numpy(w["phi0"]).pin_memory()
+        phi_in = phi_h.to(device)
+        om = torch.from_numpy(w["omega"]).to(device)
+        phi_out = torch.empty_like(phi_in)
+
+        def step():
+            ens.run_kuramoto(0, S, phi_in, phi_out, om)
+
+        def step_e2e():
+            phi_in.copy_(phi_h, non_blocking=True)
+            step()
+            return ens.observables()
+
+        h2d = phi_h.numel() * 4
+        d2h = 40 * (S // w["sample_every"] + 1)
+        units = float(N * R * S)
+        metric = "oscillator-steps/sec"
+        flop_per_launch = 2.0 * N * (2 * R) * N  # one GEMM K . [sin | cos]
+        launches_per_step = 4 * S + S // w["sample_every"] + 4
+        cfg = {"workload": "kuramoto_general_%s_N%d_R%d" % ("bf16_tcgen05" if tc else "fp32_cudacore", N, R),
+               "steps_per_bench_step": S, "K0": w["K0"], "D": w["D"], "dt": w["dt"],
+               "gemm": "M=%d N=%d K=%d per stage, 2 per step" % (N, 2 * R, N),
+               "l2": "K matrix %d MiB streams each GEMM; flushed between steps (256 MiB write)"
+                     % (N * N * (2 if tc else 4) >> 20)}
 
     # warm-up (also captures the graph)
     for _ in range(max(args.warmup, 0)):
@@ -241,7 +291,7 @@ def run_ours(args, rank, world, device):
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        kernel_ms.append(ens.last_kernel_ms())
+        kernel_ms.append(ens.last_kernel_stats()[0])
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -264,8 +314,19 @@ def run_ours(args, rank, world, device):
     e2e = statistics.median(e2e_ms) if e2e_ms else float("nan")
 
     k_ms = statistics.mean(kernel_ms)
-    achieved = flop_per_unit * units / (k_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops(props)
+    peaks, peak_src = measured_peaks()
+    if args.workload == "kuramoto-general":
+        bound, peak = "tensor", peaks["bf16_tflops_sustained"]
+        peak_note = "bf16 dense, sustained, %s" % peak_src
+        flop_note = "2 N (2R) N FLOP per GEMM launch"
+    else:
+        bound, peak = "alu", fp32_peak_tflops(props)
+        peak_note = "%d SM x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)" % props.multi_processor_count
+        flop_note = ("2 N (2R) N FLOP per GEMM launch (FP32 FMA)" if args.workload == "kuramoto-general-fp32"
+                     else "%d FLOP per unit (paper Table 1 weighting)" % flop_per_unit)
+    if args.workload in ("sweep", "plain"):
+        flop_per_launch = flop_per_unit * units / launches_kernel
+    achieved = flop_per_launch / (k_ms * 1e-3) / 1e12
     res = {
         "metric": metric,
         "value": units * world / (ms * 1e-3),
@@ -280,12 +341,9 @@ def run_ours(args, rank, world, device):
         "dtype": "f32 (FP64 reductions)",
         "data": "synthetic (seeded; inputs.py)",
         "config": cfg,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "flop_model": "%d FLOP per unit (paper Table 1 weighting)" % flop_per_unit,
-                     "peak_source": "%d SM x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)"
-                                    % props.multi_processor_count,
-                     "kernel_ms": k_ms},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "flop_model": flop_note,
+                     "peak_source": peak_note, "kernel_ms_per_launch": k_ms},
         "e2e": {"value": units * world / (e2e * 1e-3), "unit": metric.split("/")[0] + "/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
@@ -318,6 +376,16 @@ def cpu_baseline(args, budget_s=20.0):
         return {"value": done / dt, "unit": "path-steps/s", "cores": 1, "kind": "oracle",
                 "sample": "first %d paths of each of %d points, full step counts (%.3g path-steps)"
                           % (per_point, npts, done)}
+    if args.workload.startswith("kuramoto-general"):
+        w = inputs.kuramoto_general()
+        K = w["Kmat"].astype(np.float64)
+        t0 = time.perf_counter()
+        S = 1
+        oracle.kuramoto_run(w["phi0"][0], w["omega"][0], w["D"], w["dt"], 0, S, w["seed"], 0, Kmat=K)
+        dt = time.perf_counter() - t0
+        return {"value": w["n_osc"] * S / dt, "unit": "oscillator-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "replica 0 of %d, %d step (direct FP64 sum over K_ij, N = %d)"
+                          % (w["replicas"], S, w["n_osc"])}
     w = inputs.kuramoto_uniform()
     meanfield = args.workload == "kuramoto-meanfield"
     S = 200 if meanfield else 2
@@ -347,7 +415,9 @@ def run_reference(args):
         vals.append(last["value"])
     v = statistics.mean(vals)
     metric = {"sweep": "path-steps/sec", "plain": "path-steps/sec",
-              "kuramoto-meanfield": "oscillator-steps/sec", "kuramoto-pairwise": "pair-terms/sec"}[args.workload]
+              "kuramoto-meanfield": "oscillator-steps/sec", "kuramoto-pairwise": "pair-terms/sec",
+              "kuramoto-general": "oscillator-steps/sec",
+              "kuramoto-general-fp32": "oscillator-steps/sec"}[args.workload]
     unit = last["unit"]
     res = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",

@@ -62,7 +62,9 @@ typedef enum sde_schedule {
 } sde_schedule;
 
 /* Flags for sde_config.flags. */
-#define SDE_FLAG_NO_GRAPH 1u /* launch kernels directly instead of replaying a graph */
+#define SDE_FLAG_NO_GRAPH 1u     /* launch kernels directly instead of replaying a graph */
+#define SDE_FLAG_TIME_KERNELS 2u /* Kuramoto pairwise / general: CUDA events around every
+                                    launch of the dominant kernel (stage / GEMM) */
 
 /* One parameter point of Eq. 1. */
 typedef struct sde_jj_point {
@@ -192,10 +194,15 @@ sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads,
                           int32_t *paths_per_thread);
 
 /*
- * Device time in milliseconds of the dominant kernel of the last run
- * (CUDA events recorded on the run's stream around that kernel).
- * Synchronises that stream.
+ * Device time of the dominant kernel of the last run, from CUDA events
+ * recorded on the run's stream around it: the persistent or per-point
+ * Josephson launches, the mean-field kernel, or -- with
+ * SDE_FLAG_TIME_KERNELS -- each pairwise stage / GEMM launch (mean_ms per
+ * launch, total_ms summed, launches counted).  Without that flag the
+ * Kuramoto loop is bracketed as one launch.  Synchronises that stream.
+ * sde_last_kernel_ms returns mean_ms.
  */
+sde_status sde_last_kernel_stats(sde_ctx *ctx, float *mean_ms, float *total_ms, int64_t *launches);
 sde_status sde_last_kernel_ms(sde_ctx *ctx, float *ms);
 
 /*

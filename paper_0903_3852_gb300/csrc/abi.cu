@@ -511,13 +511,24 @@ sde_status sde_get_tuning(const sde_ctx *c, int32_t *block, int32_t *ilp) {
   return SDE_OK;
 }
 
+sde_status sde_last_kernel_stats(sde_ctx *c, float *mean_ms, float *total_ms, int64_t *launches) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
+  SDE_CHECK_ARG(c->timed, "no run has been timed yet");
+  if (c->kur && kuramoto_kernel_stats(c->kur, mean_ms, total_ms, launches)) return SDE_OK;
+  float ms = 0.0f;
+  SDE_CUDA_TRY(cudaEventSynchronize(c->ev1));
+  SDE_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (mean_ms) *mean_ms = ms;
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = 1;
+  return SDE_OK;
+}
+
 sde_status sde_last_kernel_ms(sde_ctx *c, float *ms) {
   clear_error();
-  SDE_CHECK_ARG(c != nullptr && ms != nullptr, "ctx and ms must be non-NULL");
-  SDE_CHECK_ARG(c->timed, "no run has been timed yet");
-  SDE_CUDA_TRY(cudaEventSynchronize(c->ev1));
-  SDE_CUDA_TRY(cudaEventElapsedTime(ms, c->ev0, c->ev1));
-  return SDE_OK;
+  SDE_CHECK_ARG(ms != nullptr, "ms is NULL");
+  return sde_last_kernel_stats(c, ms, nullptr, nullptr);
 }
 
 sde_status sde_set_coupling(sde_ctx *c, const float *K_dev, void *stream) {

@@ -427,9 +427,43 @@ void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread) 
   if (per_thread) *per_thread = k->opt;
 }
 
+cudaError_t ktime_begin(KuramotoCtx *k, cudaStream_t s) {
+  if (!(k->flags & SDE_FLAG_TIME_KERNELS)) return cudaSuccess;
+  while ((int64_t)k->kev.size() < 2 * (k->kev_used + 1)) {
+    cudaEvent_t e;
+    const cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    k->kev.push_back(e);
+  }
+  return cudaEventRecord(k->kev[2 * k->kev_used], s);
+}
+
+cudaError_t ktime_end(KuramotoCtx *k, cudaStream_t s) {
+  if (!(k->flags & SDE_FLAG_TIME_KERNELS)) return cudaSuccess;
+  const cudaError_t err = cudaEventRecord(k->kev[2 * k->kev_used + 1], s);
+  ++k->kev_used;
+  return err;
+}
+
+bool kuramoto_kernel_stats(KuramotoCtx *k, float *mean_ms, float *total_ms, int64_t *launches) {
+  if (k->kev_used == 0) return false;
+  if (cudaEventSynchronize(k->kev[2 * k->kev_used - 1]) != cudaSuccess) return false;
+  double tot = 0.0;
+  for (int64_t i = 0; i < k->kev_used; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, k->kev[2 * i], k->kev[2 * i + 1]) != cudaSuccess) return false;
+    tot += ms;
+  }
+  if (total_ms) *total_ms = (float)tot;
+  if (mean_ms) *mean_ms = (float)(tot / (double)k->kev_used);
+  if (launches) *launches = k->kev_used;
+  return true;
+}
+
 void kuramoto_destroy(KuramotoCtx *k) {
   if (!k) return;
   cudaDeviceSynchronize();
+  for (cudaEvent_t e : k->kev) cudaEventDestroy(e);
   cudaFree(k->theta);
   cudaFree(k->theta_t);
   cudaFree(k->g1);
@@ -469,6 +503,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
   kur_to_fixed<<<cvt_grid, 256, 0, s>>>(r->phi_in_dev, k->theta, NR);
   SDE_CUDA_TRY(cudaGetLastError());
   const double inv2pi = 0.15915494309189533577;
+  k->kev_used = 0;
   SDE_CUDA_TRY(cudaEventRecord(ev0, s));
   if (k->model == SDE_KURAMOTO_MEANFIELD) {
     KurArgs a{};
@@ -508,8 +543,12 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
         ++sample;
       }
       a.n = n;
+      SDE_CUDA_TRY(ktime_begin(k, s));
       kur_pairwise_stage<0><<<grid, kPairThreads, 0, s>>>(a);
+      SDE_CUDA_TRY(ktime_end(k, s));
+      SDE_CUDA_TRY(ktime_begin(k, s));
       kur_pairwise_stage<1><<<grid, kPairThreads, 0, s>>>(a);
+      SDE_CUDA_TRY(ktime_end(k, s));
     }
     SDE_CUDA_TRY(cudaGetLastError());
     if (k->M > 0) kur_order_kernel<<<(unsigned)k->R, 256, 0, s>>>(k->theta, k->N, k->R, rbuf + sample * k->R);

@@ -384,9 +384,13 @@ sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStrea
       SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
       ++sample;
     }
+    SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 0, s));
+    SDE_CUDA_TRY(ktime_end(k, s));
     SDE_CUDA_TRY(launch_stage<0>(k, 1, r->omega_dev, n, s));
+    SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 1, s));
+    SDE_CUDA_TRY(ktime_end(k, s));
     SDE_CUDA_TRY(launch_stage<1>(k, 0, r->omega_dev, n, s));
   }
   if (k->M > 0) SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace sde {
@@ -34,7 +36,15 @@ struct KuramotoCtx {
   float *P = nullptr;             // [N][2R] GEMM output
   bool have_K = false;
   void *gemm_plan = nullptr;
+  // per-launch timing of the dominant kernel (SDE_FLAG_TIME_KERNELS)
+  std::vector<cudaEvent_t> kev;
+  int64_t kev_used = 0;
 };
+
+// Record the start / end of one launch of the dominant kernel when the
+// context times kernels; no-ops otherwise.
+cudaError_t ktime_begin(KuramotoCtx *k, cudaStream_t s);
+cudaError_t ktime_end(KuramotoCtx *k, cudaStream_t s);
 
 // Arguments of the mean-field kernel.
 struct KurArgs {

@@ -27,6 +27,7 @@ SDE_SCHED_PERSISTENT = 0
 SDE_SCHED_PLAIN = 1
 
 SDE_FLAG_NO_GRAPH = 1
+SDE_FLAG_TIME_KERNELS = 2
 
 
 class SDEError(RuntimeError):
@@ -80,6 +81,8 @@ SIGNATURES = [
     ("sde_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     ("sde_last_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    ("sde_last_kernel_stats", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)]),
     ("sde_philox4x32_10", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_box_muller", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_abi_version", ctypes.c_int32, []),
@@ -249,6 +252,12 @@ class Ensemble:
         ms = ctypes.c_float()
         _check(lib().sde_last_kernel_ms(self._h, ctypes.byref(ms)))
         return ms.value
+
+    def last_kernel_stats(self):
+        """(mean ms per launch, total ms, launches) of the dominant kernel in the last run."""
+        m, t, n = ctypes.c_float(), ctypes.c_float(), ctypes.c_int64()
+        _check(lib().sde_last_kernel_stats(self._h, ctypes.byref(m), ctypes.byref(t), ctypes.byref(n)))
+        return m.value, t.value, n.value
 
     def close(self):
         if getattr(self, "_h", None):
