@@ -277,6 +277,56 @@ sde_status sde_josephson_run_noalloc(const sde_jj_point *point_host, int32_t ste
                                      int32_t *w_out_dev, double *vsum_out_dev, sde_obs_row *obs_dev,
                                      void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Learned surrogate of <<v>> (not in the paper).                          */
+/*                                                                         */
+/* An ensemble of n_members multilayer perceptrons n_in -> hidden (x      */
+/* n_hidden layers, SiLU) -> 1, mapping the parameters of Eq. 1 to the     */
+/* time-averaged velocity <<v>> of Sec. 5.  FP32 master weights and Adam   */
+/* moments; every GEMM takes BF16 operands (weights and activations        */
+/* rounded from FP32) and accumulates in FP32.  The ensemble spread is the  */
+/* network's own error estimate.  Parameters of one member are stored      */
+/* flat as [W1, b1, W2, b2, ..., W_L, b_L], W_l row-major (out, in).       */
+/* ---------------------------------------------------------------------- */
+typedef struct sde_mlp sde_mlp; /* opaque */
+
+typedef struct sde_mlp_config {
+  int32_t n_in;      /* inputs, 1..8 (the surrogate uses 5)                 */
+  int32_t hidden;    /* width of every hidden layer, multiple of 64, <= 1024 */
+  int32_t n_hidden;  /* hidden layers, 1..8                                 */
+  int32_t n_members; /* ensemble size, 1..16                                */
+  int64_t max_batch; /* largest batch of any call, >= 1                     */
+  float lr, beta1, beta2, eps; /* Adam (Kingma & Ba, Algorithm 1)          */
+  uint64_t seed;     /* initial weights: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from Philox */
+  /* feature map of sde_mlp_features: feature k = 2 (p_k - lo_k) / (hi_k - lo_k) - 1
+     for p = (a, omega, f, gamma, log10 D) */
+  float lo[5], hi[5];
+} sde_mlp_config;
+
+sde_status sde_mlp_create(const sde_mlp_config *cfg, sde_mlp **out);
+void sde_mlp_destroy(sde_mlp *mlp);
+/* parameters per member */
+int64_t sde_mlp_num_params(const sde_mlp *mlp);
+/* copy one member's FP32 parameters in / out (device arrays of num_params) */
+sde_status sde_mlp_set_params(sde_mlp *mlp, int32_t member, const float *params_dev, void *stream);
+sde_status sde_mlp_get_params(sde_mlp *mlp, int32_t member, float *params_dev, void *stream);
+/* features [n][5] from Eq. 1 parameter points (device array of sde_jj_point) */
+sde_status sde_mlp_features(sde_mlp *mlp, const sde_jj_point *points_dev, int64_t n, float *X_dev,
+                            void *stream);
+/* forward pass of every member: mean_dev[b] = ensemble mean, spread_dev[b]
+   = ensemble standard deviation (NULL allowed); X_dev [B][n_in] FP32 */
+sde_status sde_mlp_forward(sde_mlp *mlp, const float *X_dev, int64_t B, float *mean_dev,
+                           float *spread_dev, void *stream);
+/* gradient of the mean-squared error of one member: grad_dev[num_params],
+   loss_dev[1] (both device, FP32) */
+sde_status sde_mlp_grad(sde_mlp *mlp, int32_t member, const float *X_dev, const float *y_dev,
+                        int64_t B, float *grad_dev, float *loss_dev, void *stream);
+/* change the Adam step size (learning-rate schedules); lr > 0 */
+sde_status sde_mlp_set_lr(sde_mlp *mlp, float lr);
+/* one Adam step of every member on the same batch; loss_dev[n_members] or NULL */
+sde_status sde_mlp_train_step(sde_mlp *mlp, const float *X_dev, const float *y_dev, int64_t B,
+                              float *loss_dev, void *stream);
+
 /* Version of this ABI (major * 100 + minor). */
 int32_t sde_abi_version(void);
 

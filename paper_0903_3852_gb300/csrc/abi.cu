@@ -165,9 +165,10 @@ cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
 }
 
 sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp, int block,
-                      bool time_it, bool capturing = false) {
+                      bool time_it, bool capturing = false, int32_t unit_cap = 0) {
   JJLaunchArgs a = jj_args(c, r, ilp);
   const JJUnitList &L = c->units[ilp];
+  if (unit_cap > 0 && a.unit_end > unit_cap) a.unit_end = unit_cap;
   if (time_it) SDE_CUDA_TRY(record(c->ev0, s, capturing));
   if (c->cfg.schedule == SDE_SCHED_PERSISTENT) {
     if (L.n_units > 0) {
@@ -191,8 +192,11 @@ sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp
   return SDE_OK;
 }
 
-// Time each candidate launch shape on a short run over every point and keep
-// the fastest.  Uses scratch state, so the caller's buffers are untouched.
+constexpr int32_t kTunePaths = 786432;
+
+// Time each candidate launch shape on a short run over the leading units of
+// the work list and keep the fastest.  Uses scratch state, so the caller's
+// buffers are untouched.
 sde_status jj_autotune(sde_ctx *c) {
   std::vector<std::pair<int, int>> cand;
   const bool fixed_block = c->cfg.block_threads > 0;
@@ -220,7 +224,7 @@ sde_status jj_autotune(sde_ctx *c) {
     c->ilp = cand[0].second;
     return SDE_OK;
   }
-  const int64_t np = std::max<int64_t>(c->total_paths, 1);
+  const int64_t np = std::max<int64_t>(std::min<int64_t>(c->total_paths, 1ll << 40), 1);
   float *x = nullptr, *v = nullptr;
   int32_t *w = nullptr;
   double *vs = nullptr;
@@ -254,7 +258,9 @@ sde_status jj_autotune(sde_ctx *c) {
     for (auto &cd : cand) {
       float ms_min = 1e30f;
       for (int rep = 0; rep < 3 && st == SDE_OK; ++rep) {
-        st = jj_enqueue(c, &r, s, cd.second, cd.first, true);
+        // the first ~786k paths of the longest-first list (the same paths for
+        // every candidate): enough to fill the GPU many times over
+        st = jj_enqueue(c, &r, s, cd.second, cd.first, true, false, kTunePaths / (32 * cd.second));
         if (st != SDE_OK) break;
         if ((e = cudaEventSynchronize(c->ev1)) != cudaSuccess) {
           fail(e, "autotune sync");

@@ -67,6 +67,13 @@ class ObsRow(ctypes.Structure):
                 ("count", ctypes.c_double), ("t", ctypes.c_double)]
 
 
+class MlpConfig(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("hidden", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
+                ("n_members", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("lo", ctypes.c_float * 5), ("hi", ctypes.c_float * 5)]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported symbol declared in include/sde.h
@@ -87,6 +94,16 @@ SIGNATURES = [
     ("sde_box_muller", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_abi_version", ctypes.c_int32, []),
     ("sde_set_coupling", ctypes.c_int, [_VP, _VP, _VP]),
+    ("sde_mlp_create", ctypes.c_int, [ctypes.POINTER(MlpConfig), ctypes.POINTER(_VP)]),
+    ("sde_mlp_destroy", None, [_VP]),
+    ("sde_mlp_num_params", ctypes.c_int64, [_VP]),
+    ("sde_mlp_set_params", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP]),
+    ("sde_mlp_get_params", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP]),
+    ("sde_mlp_features", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP]),
+    ("sde_mlp_forward", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    ("sde_mlp_grad", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
+    ("sde_mlp_train_step", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, _VP]),
+    ("sde_mlp_set_lr", ctypes.c_int, [_VP, ctypes.c_float]),
     ("sde_kuramoto_coupling", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("sde_josephson_run_noalloc", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
@@ -289,3 +306,85 @@ def josephson_run_noalloc(point, steps_per_period, n_paths, total_steps, seed, n
         ctypes.byref(p), steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
         _ptr(x_in), _ptr(v_in), _ptr(w_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(w_out),
         _ptr(vsum_out), _ptr(obs_out), _stream(stream)))
+
+
+SURROGATE_BOX = ((0.0, 8.0), (1.0, 10.0), (0.0, 1.0), (0.5, 2.0), (-4.0, -1.0))  # a, omega, f, gamma, log10 D
+
+
+class Mlp:
+    """An sde_mlp: ensemble of surrogate networks with the library's own
+    forward, backward and Adam kernels."""
+
+    def __init__(self, n_in=5, hidden=256, n_hidden=3, members=4, max_batch=4096, lr=1e-3, beta1=0.9,
+                 beta2=0.999, eps=1e-8, seed=0, box=SURROGATE_BOX):
+        c = MlpConfig()
+        c.n_in, c.hidden, c.n_hidden, c.n_members, c.max_batch = n_in, hidden, n_hidden, members, max_batch
+        c.lr, c.beta1, c.beta2, c.eps, c.seed = lr, beta1, beta2, eps, seed
+        for k, (lo, hi) in enumerate(box):
+            c.lo[k], c.hi[k] = lo, hi
+        h = _VP()
+        _check(lib().sde_mlp_create(ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+        self.cfg = c
+        self.members = members
+        self.max_batch = max_batch
+        self.n_params = lib().sde_mlp_num_params(h)
+
+    def set_params(self, member, p, stream=None):
+        _check(lib().sde_mlp_set_params(self._h, member, _ptr(p), _stream(stream)))
+
+    def get_params(self, member, stream=None):
+        import torch
+        p = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(lib().sde_mlp_get_params(self._h, member, _ptr(p), _stream(stream)))
+        return p
+
+    def features(self, points_dev, stream=None):
+        """points_dev: uint8 CUDA tensor holding n sde_jj_point records -> (n, 5) features."""
+        import torch
+        n = points_dev.numel() // ctypes.sizeof(JJPoint)
+        X = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+        _check(lib().sde_mlp_features(self._h, _ptr(points_dev), n, _ptr(X), _stream(stream)))
+        return X
+
+    def forward(self, X, stream=None):
+        """X: (B, n_in) float32 CUDA -> (mean, spread), each (B,)."""
+        import torch
+        B = X.shape[0]
+        mean = torch.empty(B, dtype=torch.float32, device="cuda")
+        spread = torch.empty(B, dtype=torch.float32, device="cuda")
+        _check(lib().sde_mlp_forward(self._h, _ptr(X), B, _ptr(mean), _ptr(spread), _stream(stream)))
+        return mean, spread
+
+    def grad(self, member, X, y, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(lib().sde_mlp_grad(self._h, member, _ptr(X), _ptr(y), X.shape[0], _ptr(g), _ptr(loss),
+                                  _stream(stream)))
+        return g, loss
+
+    def set_lr(self, lr):
+        _check(lib().sde_mlp_set_lr(self._h, lr))
+
+    def train_step(self, X, y, loss=None, stream=None):
+        _check(lib().sde_mlp_train_step(self._h, _ptr(X), _ptr(y), X.shape[0], _ptr(loss), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sde_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def points_to_device(points):
+    """Pack a list of parameter dicts into a CUDA uint8 tensor of sde_jj_point records."""
+    import torch
+    arr = (JJPoint * len(points))(*[JJPoint(p["gamma"], p["a"], p["omega"], p["f"], p["D"]) for p in points])
+    buf = bytearray(arr)
+    return torch.frombuffer(buf, dtype=torch.uint8).clone().cuda()
