@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise",
-                             "kuramoto-general", "kuramoto-general-fp32"])
+                             "kuramoto-general", "kuramoto-general-fp32", "surrogate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairwise-steps", type=int, default=200,
                     help="steps per bench step of the pairwise Kuramoto workload")
@@ -428,6 +428,89 @@ def run_reference(args):
     return res
 
 
+def run_surrogate(args, device):
+    """The learned surrogate of <<v>>: labels from the sweep engine (10^5 points x
+    2048 paths x 2e4 steps), an ensemble of 4 networks trained by the library's
+    kernels, calibration, then one bench step = answering 10^4 held-out points
+    (network where its predicted error <= 1e-2, simulator at 8192 paths elsewhere)."""
+    import torch
+    from paper_0903_3852_gb300 import build as sde_build
+    from paper_0903_3852_gb300 import surrogate
+
+    sde_build.build()
+    props = torch.cuda.get_device_properties(device)
+    steps, tol = 20_000, 1e-2
+    train = inputs.surrogate_points(100_000, seed=6)
+    y, se, t_lab = surrogate.simulate(train, 2048, steps, seed=6)
+    label_units = len(train) * 2048.0 * steps
+    sur = surrogate.Surrogate(members=4, max_batch=16384, lr=2e-3, seed=3)
+    t0 = time.perf_counter()
+    sur.fit(train[:90_000], y[:90_000], epochs=120, batch=1024)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    sur.calibrate(train[90_000:], y[90_000:])
+    evalp = inputs.surrogate_points(10_000, seed=7)
+    ref, ref_se, t_ref = surrogate.simulate(evalp, 8192, steps, seed=7)
+    # inference throughput at batch 10^4 (features + 4 networks + spread)
+    X = sur.features(evalp)
+    for _ in range(3):
+        sur.mlp.forward(X)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        sur.mlp.forward(X)
+    torch.cuda.synchronize()
+    mlp_pps = 10 * len(evalp) / (time.perf_counter() - t0)
+    for _ in range(max(args.warmup, 0)):
+        out = sur.answer(evalp, tol, 8192, steps, seed=8)
+    clocks = ClockSampler(device)
+    clocks.start()
+    times, kms = [], []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = sur.answer(evalp, tol, 8192, steps, seed=8 + i)
+        times.append(time.perf_counter() - t0)
+        kms.append(surrogate.simulate.last_kernel_ms)
+    clk = clocks.stop()
+    err = np.abs(out["value"] - ref)
+    ans = ~out["fallback"]
+    ok = err <= tol + 3.0 * np.hypot(ref_se, np.where(ans, 0.0, out["predicted_error"]))
+    t_step = statistics.mean(times)
+    fb_units = float(out["fallback"].sum()) * 8192.0 * steps
+    k_ms = statistics.mean(kms)
+    achieved = PAPER_FLOP_PER_STEP * fb_units / (k_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(props)
+    return {
+        "metric": "points/sec", "value": len(evalp) / t_step, "unit": "points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 simulator, bf16 network (fp32 master)",
+        "data": "synthetic (seeded; inputs.py)",
+        "config": {"workload": "surrogate_10k_heldout", "train_points": 100_000, "label_paths": 2048,
+                   "steps": steps, "fallback_paths": 8192, "tol": tol, "members": 4,
+                   "net": "5-256-256-256-1 SiLU"},
+        "surrogate": {"label_seconds": t_lab, "label_points_per_sec_2048_paths": len(train) / t_lab,
+                      "label_path_steps_per_sec": label_units / t_lab, "fit_seconds": t_fit,
+                      "mlp_points_per_sec": mlp_pps,
+                      "simulator_points_per_sec_8192_paths": len(evalp) / t_ref,
+                      "answered_by_network": float(ans.mean()),
+                      "within_tol_all": float(ok.mean()),
+                      "within_tol_network_answers": float(ok[ans].mean()) if ans.any() else None,
+                      "median_abs_err_network_answers": float(np.median(err[ans])) if ans.any() else None,
+                      "gain_vs_simulator_only": t_ref / t_step},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "flop_model": "79 FLOP per path-step (paper Table 1 weighting), fallback simulation",
+                     "peak_source": "%d SM x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)"
+                                    % props.multi_processor_count, "kernel_ms_per_launch": k_ms},
+        "e2e": {"value": len(evalp) / t_step, "unit": "points/s", "h2d_bytes_per_step": 40 * len(evalp),
+                "d2h_bytes_per_step": 8 * len(evalp)},
+        # per step: features 1 + 4 members x (2 casts + 4 GEMMs) + spread 1; the fallback
+        # simulation: prepare 1 + autotune 6 x 3 x 2 + persistent kernel + finalize
+        "gpu_launches": (26 + 1 + 36 + 2) * args.steps, "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -443,6 +526,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "surrogate":
+        res = run_surrogate(args, local)
+        if rank == 0:
+            print(json.dumps(res))
+        return
     res, ens = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:

@@ -326,6 +326,10 @@ sde_status sde_mlp_set_lr(sde_mlp *mlp, float lr);
 /* one Adam step of every member on the same batch; loss_dev[n_members] or NULL */
 sde_status sde_mlp_train_step(sde_mlp *mlp, const float *X_dev, const float *y_dev, int64_t B,
                               float *loss_dev, void *stream);
+/* one Adam step of every member on its own batch (bootstrap ensembles):
+   X_dev [n_members][B][n_in], y_dev [n_members][B] */
+sde_status sde_mlp_train_step_members(sde_mlp *mlp, const float *X_dev, const float *y_dev, int64_t B,
+                                      float *loss_dev, void *stream);
 
 /* Version of this ABI (major * 100 + minor). */
 int32_t sde_abi_version(void);

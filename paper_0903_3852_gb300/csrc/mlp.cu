@@ -504,14 +504,18 @@ sde_status sde_mlp_set_lr(sde_mlp *q, float lr) {
   return SDE_OK;
 }
 
-sde_status sde_mlp_train_step(sde_mlp *q, const float *X, const float *y, int64_t B, float *loss, void *stream) {
+static sde_status mlp_train(sde_mlp *q, const float *X, const float *y, int64_t B, float *loss, void *stream,
+                            bool per_member) {
   clear_error();
   SDE_CHECK_ARG(q != nullptr, "mlp is NULL");
   SDE_CHECK_ARG(B >= 1 && B <= q->cfg.max_batch, "batch must be in [1, max_batch]");
   SDE_CHECK_ARG(X && y, "X and y must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
   for (int mm = 0; mm < q->cfg.n_members; ++mm) {
-    sde_status st = mlp_grad_member(q, mm, X, y, B, q->grad + (int64_t)mm * q->P, loss ? loss + mm : nullptr, s);
+    const int64_t xo = per_member ? (int64_t)mm * B * q->cfg.n_in : 0;
+    const int64_t yo = per_member ? (int64_t)mm * B : 0;
+    sde_status st = mlp_grad_member(q, mm, X + xo, y + yo, B, q->grad + (int64_t)mm * q->P,
+                                    loss ? loss + mm : nullptr, s);
     if (st != SDE_OK) return st;
   }
   q->step += 1;
@@ -525,6 +529,15 @@ sde_status sde_mlp_train_step(sde_mlp *q, const float *X, const float *y, int64_
   adam_kernel<<<grid1(n), 256, 0, s>>>(q->params, q->grad, q->m, q->v, n, lr_t, (float)b1, (float)b2, eps_t);
   SDE_CUDA_TRY(cudaGetLastError());
   return SDE_OK;
+}
+
+sde_status sde_mlp_train_step(sde_mlp *q, const float *X, const float *y, int64_t B, float *loss, void *stream) {
+  return mlp_train(q, X, y, B, loss, stream, false);
+}
+
+sde_status sde_mlp_train_step_members(sde_mlp *q, const float *X, const float *y, int64_t B, float *loss,
+                                      void *stream) {
+  return mlp_train(q, X, y, B, loss, stream, true);
 }
 
 }  // extern "C"

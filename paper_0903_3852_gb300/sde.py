@@ -104,6 +104,7 @@ SIGNATURES = [
     ("sde_mlp_grad", ctypes.c_int, [_VP, ctypes.c_int32, _VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
     ("sde_mlp_train_step", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, _VP]),
     ("sde_mlp_set_lr", ctypes.c_int, [_VP, ctypes.c_float]),
+    ("sde_mlp_train_step_members", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, _VP]),
     ("sde_kuramoto_coupling", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("sde_josephson_run_noalloc", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
@@ -369,6 +370,11 @@ class Mlp:
 
     def train_step(self, X, y, loss=None, stream=None):
         _check(lib().sde_mlp_train_step(self._h, _ptr(X), _ptr(y), X.shape[0], _ptr(loss), _stream(stream)))
+
+    def train_step_members(self, X, y, loss=None, stream=None):
+        """X: (members, B, n_in), y: (members, B): one batch per member."""
+        _check(lib().sde_mlp_train_step_members(self._h, _ptr(X), _ptr(y), X.shape[1], _ptr(loss),
+                                                _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None):

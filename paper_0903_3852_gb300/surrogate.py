@@ -45,8 +45,9 @@ def simulate(points, paths, steps, seed, stream=None, init_seed=None):
     vs = torch.empty(total, dtype=torch.float64, device="cuda")
     ens.run_josephson(0, steps, x0, v0, x0, v0, w, vs, stream=stream)
     obs = ens.observables()
-    ens.close()
     dt = time.perf_counter() - t0
+    simulate.last_kernel_ms = ens.last_kernel_ms()
+    ens.close()
     return obs["mean"].copy(), obs["se"].copy(), dt
 
 
@@ -61,21 +62,26 @@ class Surrogate:
         return self.mlp.features(sde.points_to_device(points))
 
     def fit(self, points, y, epochs=60, batch=1024, seed=0, lr_final=1e-5):
-        """Train every member on (features(points), y); returns the last losses."""
+        """Train every member on its own bootstrap resample of (features(points),
+        y) -- the spread of such an ensemble tracks its error; returns the
+        last losses."""
         X = self.features(points)
         yd = torch.as_tensor(np.asarray(y, dtype=np.float32)).cuda()
         n = X.shape[0]
+        M = self.mlp.members
         rng = np.random.default_rng(seed)
-        loss = torch.zeros(self.mlp.members, device="cuda")
+        boot = [rng.integers(0, n, n) for _ in range(M)]
+        loss = torch.zeros(M, device="cuda")
         steps = epochs * max(1, n // batch)
         k = 0
         for ep in range(epochs):
-            perm = torch.from_numpy(rng.permutation(n)).cuda()
+            order = [b[rng.permutation(n)] for b in boot]
             for b0 in range(0, n - batch + 1, batch):
                 # cosine decay of the step size from lr to lr_final
                 self.mlp.set_lr(lr_final + 0.5 * (self.lr - lr_final) * (1 + np.cos(np.pi * k / steps)))
-                idx = perm[b0:b0 + batch]
-                self.mlp.train_step(X[idx].contiguous(), yd[idx].contiguous(), loss)
+                idx = torch.from_numpy(np.concatenate([o[b0:b0 + batch] for o in order])).cuda()
+                self.mlp.train_step_members(X[idx].view(M, batch, -1).contiguous(),
+                                            yd[idx].view(M, batch).contiguous(), loss)
                 k += 1
         return loss.cpu().numpy()
 
@@ -89,22 +95,32 @@ class Surrogate:
             spreads.append(s)
         return torch.cat(means).cpu().numpy(), torch.cat(spreads).cpu().numpy()
 
-    def calibrate(self, points, y, coverage=0.95):
-        """Factor k with |prediction - y| <= k spread on `coverage` of the points."""
+    def calibrate(self, points, y, coverage=0.95, bins=8):
+        """Factors k with |prediction - y| <= k spread on `coverage` of the
+        calibration points, one per bin of spread (quantile bins), so that the
+        predicted error k(spread) spread adapts to regions where the spread is
+        more or less faithful.  Returns the overall factor."""
         mean, spread = self.predict(points)
         ratio = np.abs(mean - np.asarray(y)) / np.maximum(spread, 1e-12)
+        self.edges = np.quantile(spread, np.linspace(0, 1, bins + 1)[1:-1])
+        which = np.searchsorted(self.edges, spread)
+        self.kbin = np.array([np.quantile(ratio[which == b], coverage) if np.any(which == b)
+                              else np.quantile(ratio, coverage) for b in range(bins)])
         self.k = float(np.quantile(ratio, coverage))
         return self.k
 
+    def predicted_error(self, spread):
+        return self.kbin[np.searchsorted(self.edges, spread)] * spread
+
     def answer(self, points, tol, fallback_paths, steps, seed):
-        """Network prediction where k * spread <= tol, simulator elsewhere.
+        """Network prediction where its predicted error is <= tol, simulator elsewhere.
         Returns dict(value, predicted_error, fallback mask, seconds split)."""
         assert self.k is not None, "calibrate first"
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mean, spread = self.predict(points)
         t_mlp = time.perf_counter() - t0
-        perr = self.k * spread
+        perr = self.predicted_error(spread)
         fb = perr > tol
         value = mean.astype(np.float64).copy()
         t_sim = 0.0
