@@ -13,8 +13,10 @@
 //
 // Time is kept modulo the drive period as the integer k = n mod P (Sec. 5),
 // so cos(omega t_n) = cos(2 pi k / P) comes from a P-entry table in shared
-// memory.  Position is kept as x in [0, 1) plus an integer winding count, so
-// FP32 resolution does not degrade as paths run away.
+// memory.  Position is kept as x in [0, 1) plus an integer winding count
+// (folded once per group of four steps), so FP32 resolution does not degrade
+// as paths run away.  cos(2 pi x) is a branch-free minimax polynomial
+// (cos2pi below).
 //
 // The window average of v (the time-averaged velocity <<v>> of Sec. 5) is
 // summed in FP32 over blocks of 64 steps (aligned to absolute step indices)
@@ -34,23 +36,47 @@ namespace {
 
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
+// cos(2 pi x) for |x| < 2^22 without branches: with r = x - rint(x) in
+// [-1/2, 1/2] and b = 1/4 - |r| in [-1/4, 1/4], cos(2 pi x) = sin(2 pi b),
+// and sin(2 pi b) = b P(b^2) with P a degree-4 polynomial whose coefficients
+// minimise the largest absolute error on [0, 1/4] (Lawson's iteratively
+// reweighted least squares, about 3e-9 in exact arithmetic).  In FP32 the
+// error is at most 1.7e-7 (RMS 3.7e-8).  rint comes from adding and
+// subtracting 1.5 * 2^23, all on the FMA pipe.
+__device__ __forceinline__ float cos2pi(float x) {
+  const float t = (x + 12582912.0f) - 12582912.0f;
+  const float b = 0.25f - fabsf(x - t);
+  const float s = b * b;
+  float p = 39.536705f;
+  p = fmaf(p, s, -76.5497818f);
+  p = fmaf(p, s, 81.6010056f);
+  p = fmaf(p, s, -41.3416557f);
+  p = fmaf(p, s, 6.28318501f);
+  return b * p;
+}
+
+// One SRK2 step.  x is kept in [0, 1) up to the drift of the steps since the
+// last wrap (at most four steps, see jj_segment).
 template <bool ACC>
-__device__ __forceinline__ void jj_step(float &x, int &w, float &v, float &acc, float z,
-                                        const JJConsts &c, float dr0, float dr1) {
+__device__ __forceinline__ void jj_step(float &x, float &v, float &acc, float z, const JJConsts &c, float dr0,
+                                        float dr1) {
   const float nz = c.s * z;
-  const float c1 = cospif(2.0f * x);
+  const float c1 = cos2pi(x);
   const float F1 = fmaf(-kTwoPiF, c1, fmaf(-c.gamma, v, fmaf(c.a, dr0, c.f)));
   const float xt = fmaf(c.dt, v, x);
   const float vt = fmaf(c.dt, F1, v + nz);
-  const float c2 = cospif(2.0f * xt);
+  const float c2 = cos2pi(xt);
   const float F2 = fmaf(-kTwoPiF, c2, fmaf(-c.gamma, vt, fmaf(c.a, dr1, c.f)));
-  const float xn = fmaf(c.h, v + vt, x);
-  const float vn = fmaf(c.h, F1 + F2, v + nz);
-  const float fl = floorf(xn);
-  x = xn - fl;
+  x = fmaf(c.h, v + vt, x);
+  v = fmaf(c.h, F1 + F2, v + nz);
+  if (ACC) acc += v;
+}
+
+// Fold x back into [0, 1), counting whole turns in w.
+__device__ __forceinline__ void jj_wrap(float &x, int &w) {
+  const float fl = floorf(x);
+  x -= fl;
   w += (int)fl;
-  v = vn;
-  if (ACC) acc += vn;
 }
 
 // Advance ILP paths over the steps [n0, n1).  `k` is the drive-table index
@@ -78,7 +104,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
         k = (k + 1 == P) ? 0 : k + 1;
         const float dr1 = drive[k];
 #pragma unroll
-        for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], w[i], v[i], acc[i], z[i][s], c, dr0, dr1);
+        for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, dr0, dr1);
       }
     } else {
 #pragma unroll
@@ -89,10 +115,12 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
           k = (k + 1 == P) ? 0 : k + 1;
           const float dr1 = drive[k];
 #pragma unroll
-          for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], w[i], v[i], acc[i], z[i][s], c, dr0, dr1);
+          for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, dr0, dr1);
         }
       }
     }
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) jj_wrap(x[i], w[i]);
     // Flush the FP32 partial sums at absolute 64-step boundaries, so that a
     // run split at any multiple of 64 steps reproduces the unsplit sums.
     if (ACC && ((g + 1) & 15) == 0) {

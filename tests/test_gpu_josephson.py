@@ -117,16 +117,22 @@ def test_resume_is_bit_exact():
     w = inputs.josephson_plain(paths=n, steps=S)
     ens = _ens([FIG2], [n], [S])
     xa, va, wa, fa, sa, _ = jj_run(ens, w["x0"], w["v0"], 0, S)
-    # split at a multiple of 64 steps (the flush block of the window sums): bit-exact
+    # split at a multiple of 64 steps (the flush block of the window sums and a
+    # multiple of the 4-step noise group): bit-exact
     xb, vb, wb, fb, sb, _ = jj_run(ens, w["x0"], w["v0"], 0, 1216)
     xc, vc, wc, fc, sc, _ = jj_run(ens, fb, vb, 1216, S, w0=wb, vs0=sb)
     assert np.array_equal(fa, fc) and np.array_equal(va, vc)
     assert np.array_equal(wa, wc) and np.array_equal(sa, sc)
-    # any other split: the state is still bit-exact, the window sums agree to FP32 rounding
+    # any other split (damped point, where rounding differences do not grow):
+    # positions are folded into [0, 1) at the split instead of at the end of the
+    # 4-step noise group, so the runs agree to FP32 rounding
+    ens = _ens([DAMPED], [n], [S])
+    xa, va, wa, fa, sa, _ = jj_run(ens, w["x0"], w["v0"], 0, S)
     xb, vb, wb, fb, sb, _ = jj_run(ens, w["x0"], w["v0"], 0, 1203)
     xc, vc, wc, fc, sc, _ = jj_run(ens, fb, vb, 1203, S, w0=wb, vs0=sb)
-    assert np.array_equal(fa, fc) and np.array_equal(va, vc) and np.array_equal(wa, wc)
-    assert np.max(np.abs(sa - sc) / np.maximum(1.0, np.abs(sa))) <= 1e-5
+    assert mixed_rel(xc, xa).max() <= 1e-6 and mixed_rel(vc, va).max() <= 1e-6
+    # window averages (sum / window length) agree to FP32 partial-sum rounding
+    assert np.max(np.abs(sa - sc)) / (S // 2) <= 1e-7
 
 
 def test_observable_fig2_plain_matches_oracle_within_3se():
