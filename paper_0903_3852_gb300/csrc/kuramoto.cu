@@ -161,6 +161,15 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
 
 // ---- pairwise form (Alg. 3) --------------------------------------------
 
+// sin(2 pi d) for a phase difference d in turns, |d| < 2^22: d is first
+// reduced to [-1/2, 1/2] by subtracting rint(d) (computed by adding and
+// subtracting 1.5 * 2^23 on the FMA pipe), so that the one special-function
+// instruction sees an argument in [-pi, pi].
+__device__ __forceinline__ float sin2pi_diff(float d) {
+  const float r = d - ((d + 12582912.0f) - 12582912.0f);
+  return __sinf(6.28318530717958647692f * r);
+}
+
 constexpr int kPairThreads = 128;
 constexpr int kPairPerThread = 2;  // receivers per thread
 constexpr int kPairTile = kPairThreads * kPairPerThread;
@@ -197,21 +206,13 @@ __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPair
       for (int jj = 0; jj < kPairTile; ++jj) {
         const float tj = src_s[jj];
 #pragma unroll
-        for (int k = 0; k < kPairPerThread; ++k) {
-          float d = tj - ti[k];
-          d -= rintf(d);
-          acc[k] += __sinf(6.28318530717958647692f * d);
-        }
+        for (int k = 0; k < kPairPerThread; ++k) acc[k] += sin2pi_diff(tj - ti[k]);
       }
     } else {
       for (int jj = 0; jj < cnt; ++jj) {
         const float tj = src_s[jj];
 #pragma unroll
-        for (int k = 0; k < kPairPerThread; ++k) {
-          float d = tj - ti[k];
-          d -= rintf(d);
-          acc[k] += __sinf(6.28318530717958647692f * d);
-        }
+        for (int k = 0; k < kPairPerThread; ++k) acc[k] += sin2pi_diff(tj - ti[k]);
       }
     }
     __syncthreads();
