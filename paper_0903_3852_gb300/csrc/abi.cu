@@ -130,14 +130,18 @@ sde_status build_units(sde_ctx *c, int ilp) {
   return SDE_OK;
 }
 
+// Launch variants: 1, 2 = paths per thread; 11, 12 = the same with registers
+// capped at 64.  The work list depends on the paths per thread only.
+int paths_per_thread(int variant) { return variant % 10; }
+
 JJLaunchArgs jj_args(const sde_ctx *c, const sde_run_desc *r, int ilp) {
   JJLaunchArgs a{};
   a.consts = c->consts;
-  a.units = c->units[ilp].units;
+  a.units = c->units[paths_per_thread(ilp)].units;
   a.drive = c->drive;
   a.P = c->P;
   a.unit_begin = 0;
-  a.unit_end = c->units[ilp].n_units;
+  a.unit_end = c->units[paths_per_thread(ilp)].n_units;
   a.queue = nullptr;
   a.partials = c->partials;
   a.err = c->err;
@@ -152,7 +156,7 @@ JJLaunchArgs jj_args(const sde_ctx *c, const sde_run_desc *r, int ilp) {
 int persistent_grid(const sde_ctx *c, int ilp, int block) {
   const int per_sm = jj_max_blocks_per_sm(ilp, block, c->P);
   const int warps = block / 32;
-  const int need = (c->units[ilp].n_units + warps - 1) / warps;
+  const int need = (c->units[paths_per_thread(ilp)].n_units + warps - 1) / warps;
   int grid = std::max(1, per_sm) * c->sm_count;
   return std::max(1, std::min(grid, need));
 }
@@ -167,7 +171,7 @@ cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
 sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp, int block,
                       bool time_it, bool capturing = false, int32_t unit_cap = 0) {
   JJLaunchArgs a = jj_args(c, r, ilp);
-  const JJUnitList &L = c->units[ilp];
+  const JJUnitList &L = c->units[paths_per_thread(ilp)];
   if (unit_cap > 0 && a.unit_end > unit_cap) a.unit_end = unit_cap;
   if (time_it) SDE_CUDA_TRY(record(c->ev0, s, capturing));
   if (c->cfg.schedule == SDE_SCHED_PERSISTENT) {
@@ -216,7 +220,7 @@ sde_status jj_autotune(sde_ctx *c) {
   else if (c->cfg.schedule == SDE_SCHED_PLAIN)
     il.push_back(1);  // the per-path kernel of Alg. 1: one thread per path
   else
-    il = {1, 2};
+    il = {1, 2, 11, 12};
   for (int b : bl)
     for (int i : il) cand.push_back({b, i});
   if (cand.size() == 1) {
@@ -260,7 +264,8 @@ sde_status jj_autotune(sde_ctx *c) {
       for (int rep = 0; rep < 3 && st == SDE_OK; ++rep) {
         // the first ~786k paths of the longest-first list (the same paths for
         // every candidate): enough to fill the GPU many times over
-        st = jj_enqueue(c, &r, s, cd.second, cd.first, true, false, kTunePaths / (32 * cd.second));
+        st = jj_enqueue(c, &r, s, cd.second, cd.first, true, false,
+                        kTunePaths / (32 * paths_per_thread(cd.second)));
         if (st != SDE_OK) break;
         if ((e = cudaEventSynchronize(c->ev1)) != cudaSuccess) {
           fail(e, "autotune sync");

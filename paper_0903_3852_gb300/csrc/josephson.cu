@@ -57,16 +57,17 @@ __device__ __forceinline__ float cos2pi(float x) {
 
 // One SRK2 step.  x is kept in [0, 1) up to the drift of the steps since the
 // last wrap (at most four steps, see jj_segment).
+// e0, e1: the drive and bias a cos(omega t) + f at t_n and t_{n+1}.
 template <bool ACC>
-__device__ __forceinline__ void jj_step(float &x, float &v, float &acc, float z, const JJConsts &c, float dr0,
-                                        float dr1) {
+__device__ __forceinline__ void jj_step(float &x, float &v, float &acc, float z, const JJConsts &c, float e0,
+                                        float e1) {
   const float nz = c.s * z;
   const float c1 = cos2pi(x);
-  const float F1 = fmaf(-kTwoPiF, c1, fmaf(-c.gamma, v, fmaf(c.a, dr0, c.f)));
+  const float F1 = fmaf(-kTwoPiF, c1, fmaf(-c.gamma, v, e0));
   const float xt = fmaf(c.dt, v, x);
   const float vt = fmaf(c.dt, F1, v + nz);
   const float c2 = cos2pi(xt);
-  const float F2 = fmaf(-kTwoPiF, c2, fmaf(-c.gamma, vt, fmaf(c.a, dr1, c.f)));
+  const float F2 = fmaf(-kTwoPiF, c2, fmaf(-c.gamma, vt, e1));
   x = fmaf(c.h, v + vt, x);
   v = fmaf(c.h, F1 + F2, v + nz);
   if (ACC) acc += v;
@@ -98,24 +99,39 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
     for (int i = 0; i < ILP; ++i) gauss4((uint32_t)g, pid[i], point, kTagJosephson, key, z[i]);
     const int64_t base = g << 2;
     if (base >= n0 && base + 4 <= n1) {
+      // full group: drive values at t_{4g} .. t_{4g+4}
+      float e[5];
+      if ((P & 3) == 0) {
+        // k is a multiple of 4 here; the table is padded by 4 entries
+        const float4 d = *reinterpret_cast<const float4 *>(drive + k);
+        e[0] = fmaf(c.a, d.x, c.f);
+        e[1] = fmaf(c.a, d.y, c.f);
+        e[2] = fmaf(c.a, d.z, c.f);
+        e[3] = fmaf(c.a, d.w, c.f);
+        e[4] = fmaf(c.a, drive[k + 4], c.f);
+        k += 4;
+        if (k == P) k = 0;
+      } else {
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const float dr0 = drive[k];
-        k = (k + 1 == P) ? 0 : k + 1;
-        const float dr1 = drive[k];
-#pragma unroll
-        for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, dr0, dr1);
+        for (int s = 0; s < 5; ++s) {
+          e[s] = fmaf(c.a, drive[k], c.f);
+          if (s < 4) k = (k + 1 == P) ? 0 : k + 1;
+        }
       }
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, e[s], e[s + 1]);
     } else {
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
         const int64_t n = base + s;
         if (n >= n0 && n < n1) {
-          const float dr0 = drive[k];
+          const float e0 = fmaf(c.a, drive[k], c.f);
           k = (k + 1 == P) ? 0 : k + 1;
-          const float dr1 = drive[k];
+          const float e1 = fmaf(c.a, drive[k], c.f);
 #pragma unroll
-          for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, dr0, dr1);
+          for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, e0, e1);
         }
       }
     }
@@ -225,9 +241,12 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
 }
 
 template <int ILP>
-__global__ void __launch_bounds__(512) jj_kernel(const JJLaunchArgs A) {
-  extern __shared__ float drive_s[];
-  for (int i = threadIdx.x; i < A.P; i += blockDim.x) drive_s[i] = A.drive[i];
+__device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
+  // drive table cos(2 pi k / P), k = 0 .. P + 3 (four entries of padding
+  // repeat the start of the period), 16-byte aligned
+  extern __shared__ float4 drive_s4[];
+  float *drive_s = reinterpret_cast<float *>(drive_s4);
+  for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x) drive_s[i] = A.drive[i % A.P];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
@@ -244,6 +263,19 @@ __global__ void __launch_bounds__(512) jj_kernel(const JJLaunchArgs A) {
     const int u = A.unit_begin + blockIdx.x * warps + (threadIdx.x >> 5);
     if (u < A.unit_end) jj_unit<ILP>(A, u, drive_s, lane);
   }
+}
+
+template <int ILP>
+__global__ void __launch_bounds__(512) jj_kernel(const JJLaunchArgs A) {
+  jj_kernel_body<ILP>(A);
+}
+
+// The same kernel with registers capped at 64 per thread (blocks of up to 512
+// threads, two per SM): more resident warps for more spills; the autotuner
+// picks.
+template <int ILP>
+__global__ void __launch_bounds__(512, 2) jj_kernel_cap64(const JJLaunchArgs A) {
+  jj_kernel_body<ILP>(A);
 }
 
 __global__ void jj_prepare_kernel(const sde_jj_point *pts, int n_points, int P,
@@ -327,9 +359,14 @@ __global__ void box_muller_fill_kernel(const uint4 *ctr, uint2 key, float4 *z, i
   }
 }
 
-template <int ILP>
-void *jj_kernel_ptr() {
-  return (void *)jj_kernel<ILP>;
+void *jj_kernel_ptr(int variant) {
+  switch (variant) {
+    case 1: return (void *)jj_kernel<1>;
+    case 2: return (void *)jj_kernel<2>;
+    case 11: return (void *)jj_kernel_cap64<1>;
+    case 12: return (void *)jj_kernel_cap64<2>;
+  }
+  return nullptr;
 }
 
 }  // namespace
@@ -343,21 +380,24 @@ cudaError_t jj_prepare(const sde_jj_point *points_dev, int n_points, int P, cons
   return cudaGetLastError();
 }
 
+// `ilp` encodes the variant: 1, 2 = paths per thread; +10 = registers capped at 64.
 cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(float) * (size_t)a.P;
-  if (ilp == 1)
-    jj_kernel<1><<<grid, block, smem, s>>>(a);
-  else if (ilp == 2)
-    jj_kernel<2><<<grid, block, smem, s>>>(a);
-  else
-    return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * (size_t)(a.P + 4);
+  switch (ilp) {
+    case 1: jj_kernel<1><<<grid, block, smem, s>>>(a); break;
+    case 2: jj_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 11: jj_kernel_cap64<1><<<grid, block, smem, s>>>(a); break;
+    case 12: jj_kernel_cap64<2><<<grid, block, smem, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 int jj_max_blocks_per_sm(int ilp, int block, int P) {
   int nb = 0;
-  void *k = ilp == 1 ? jj_kernel_ptr<1>() : jj_kernel_ptr<2>();
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, sizeof(float) * P) != cudaSuccess)
+  void *k = jj_kernel_ptr(ilp);
+  if (!k) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, sizeof(float) * (P + 4)) != cudaSuccess)
     return 0;
   return nb;
 }
@@ -423,10 +463,11 @@ struct NoallocArgs {
 // One warp per 32 paths, one path per thread: the same arithmetic and the same
 // unit decomposition as the plain schedule with one path per thread.
 __global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
-  extern __shared__ float drive_s[];
+  extern __shared__ float4 drive_s4[];
+  float *drive_s = reinterpret_cast<float *>(drive_s4);
   const double dt = 2.0 * 3.14159265358979323846 / (A.p.omega * (double)A.P);
-  for (int i = threadIdx.x; i < A.P; i += blockDim.x)
-    drive_s[i] = (float)cospi(2.0 * (double)i / (double)A.P);
+  for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x)
+    drive_s[i] = (float)cospi(2.0 * (double)(i % A.P) / (double)A.P);
   __syncthreads();
   JJConsts c;
   c.gamma = (float)A.p.gamma;
@@ -577,7 +618,7 @@ extern "C" sde_status sde_josephson_run_noalloc(const sde_jj_point *point, int32
   a.partials = partials;
   const int n_units = (int)((n_paths + 31) / 32);
   if (n_units > 0) {
-    jj_noalloc_kernel<<<(n_units + 7) / 8, 256, sizeof(float) * steps_per_period, s>>>(a);
+    jj_noalloc_kernel<<<(n_units + 7) / 8, 256, sizeof(float) * (steps_per_period + 4), s>>>(a);
     SDE_CUDA_TRY(cudaGetLastError());
   }
   const double dt = 2.0 * 3.14159265358979323846 / (point->omega * (double)steps_per_period);

@@ -47,69 +47,63 @@ __device__ __forceinline__ __nv_bfloat16 to_op<__nv_bfloat16>(float v) {
   return __float2bfloat16_rn(v);
 }
 
-// Operand rows [2r] = sin, [2r+1] = cos of every phase.
+// Operand rows [2r] = sin, [2r+1] = cos of every phase.  Grid: (N / 256, R).
 template <typename T>
-__global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N, int64_t R) {
-  const int64_t total = N * R;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / N, i = idx - r * N;
-    float s, c;
-    sincospif(2.0f * signed_turns(theta[idx]), &s, &c);
-    op[(2 * r) * N + i] = to_op<T>(s);
-    op[(2 * r + 1) * N + i] = to_op<T>(c);
-  }
+__global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N) {
+  const int64_t r = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float s, c;
+  sincospif(2.0f * signed_turns(theta[r * N + i]), &s, &c);
+  op[(2 * r) * N + i] = to_op<T>(s);
+  op[(2 * r + 1) * N + i] = to_op<T>(c);
 }
 
 // One SRK2 stage for every (replica, oscillator) from the GEMM output Dt.
 // STAGE 0: predictor theta~ = theta + dt/(2 pi) (omega + g1) + sqrt(2 D dt)/(2 pi) psi
 // STAGE 1: corrector theta' = theta + dt/(2 pi) (omega + (g1 + g2) / 2) + ... psi
+// The step's Gaussian psi is drawn in stage 0 and kept for stage 1.
+// Grid: (N / 256, R).
 template <int STAGE, typename T>
 __global__ void kg_stage_kernel(const float *__restrict__ Dt, uint32_t *theta, uint32_t *theta_t, float *g1,
-                                const float *__restrict__ omega, T *op_next, int64_t N, int64_t R, int64_t n,
+                                float *psi_buf, const float *__restrict__ omega, T *op_next, int64_t N, int64_t n,
                                 float wscale, float kc, float kh, float sc, uint64_t seed) {
-  const int64_t total = N * R;
-  const uint2 key = seed_to_key(seed);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / N, i = idx - r * N;
-    const uint32_t th_i = STAGE == 0 ? theta[idx] : theta_t[idx];
-    float s, c;
-    sincospif(2.0f * signed_turns(th_i), &s, &c);
-    const float g = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
-    float z[4];
-    gauss4((uint32_t)(n >> 2), (uint32_t)i, (uint32_t)r, kTagKuramoto, key, z);
-    const float psi = pick4(z, (int)(n & 3));
-    const float wdt = omega[idx] * wscale;
-    uint32_t out;
-    if (STAGE == 0) {
-      const float d1 = fmaf(sc, psi, fmaf(kc, g, wdt));
-      out = theta[idx] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
-      theta_t[idx] = out;
-      g1[idx] = g;
-    } else {
-      const float d = fmaf(sc, psi, fmaf(kh, g1[idx] + g, wdt));
-      out = theta[idx] + (uint32_t)__float2int_rn(d * 4294967296.0f);
-      theta[idx] = out;
-    }
-    float so, co;
-    sincospif(2.0f * signed_turns(out), &so, &co);
-    op_next[(2 * r) * N + i] = to_op<T>(so);
-    op_next[(2 * r + 1) * N + i] = to_op<T>(co);
+  const int64_t r = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t idx = r * N + i;
+  const uint32_t th_i = STAGE == 0 ? theta[idx] : theta_t[idx];
+  float s, c;
+  sincospif(2.0f * signed_turns(th_i), &s, &c);
+  const float g = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
+  const float wdt = omega[idx] * wscale;
+  uint32_t out;
+  if (STAGE == 0) {
+    const float psi = gauss1(n, (uint32_t)i, (uint32_t)r, kTagKuramoto, seed_to_key(seed));
+    psi_buf[idx] = psi;
+    const float d1 = fmaf(sc, psi, fmaf(kc, g, wdt));
+    out = theta[idx] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+    theta_t[idx] = out;
+    g1[idx] = g;
+  } else {
+    const float d = fmaf(sc, psi_buf[idx], fmaf(kh, g1[idx] + g, wdt));
+    out = theta[idx] + (uint32_t)__float2int_rn(d * 4294967296.0f);
+    theta[idx] = out;
   }
+  float so, co;
+  sincospif(2.0f * signed_turns(out), &so, &co);
+  op_next[(2 * r) * N + i] = to_op<T>(so);
+  op_next[(2 * r + 1) * N + i] = to_op<T>(co);
 }
 
 // Coupling sums alone: out[r][i] = cos x_i Dt[2r][i] - sin x_i Dt[2r+1][i].
-__global__ void kg_coupling_kernel(const float *__restrict__ Dt, const uint32_t *theta, float *out, int64_t N,
-                                   int64_t R) {
-  const int64_t total = N * R;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / N, i = idx - r * N;
-    float s, c;
-    sincospif(2.0f * signed_turns(theta[idx]), &s, &c);
-    out[idx] = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
-  }
+__global__ void kg_coupling_kernel(const float *__restrict__ Dt, const uint32_t *theta, float *out, int64_t N) {
+  const int64_t r = blockIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  float s, c;
+  sincospif(2.0f * signed_turns(theta[r * N + i]), &s, &c);
+  out[r * N + i] = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
 }
 
 __global__ void kg_to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int64_t n) {
@@ -270,12 +264,13 @@ cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+dim3 grid_nr(const KuramotoCtx *k) { return dim3((unsigned)((k->N + 255) / 256), (unsigned)k->R); }
+
 cudaError_t launch_operand(KuramotoCtx *k, int which, cudaStream_t s) {
-  const int grid = grid_for(k->N * k->R, k->sm_count);
   if (is_tc(k))
-    kg_operand_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(k->theta, (__nv_bfloat16 *)op_buf(k, which), k->N, k->R);
+    kg_operand_kernel<__nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(k->theta, (__nv_bfloat16 *)op_buf(k, which), k->N);
   else
-    kg_operand_kernel<float><<<grid, 256, 0, s>>>(k->theta, (float *)op_buf(k, which), k->N, k->R);
+    kg_operand_kernel<float><<<grid_nr(k), 256, 0, s>>>(k->theta, (float *)op_buf(k, which), k->N);
   return cudaGetLastError();
 }
 
@@ -286,15 +281,14 @@ cudaError_t launch_stage(KuramotoCtx *k, int next, const float *omega, int64_t n
   const float kc = (float)(k->dt * inv2pi);
   const float kh = (float)(0.5 * k->dt * inv2pi);
   const float sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
-  const int grid = grid_for(k->N * k->R, k->sm_count);
   if (is_tc(k))
-    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid, 256, 0, s>>>(
-        k->P, k->theta, k->theta_t, k->g1, omega, (__nv_bfloat16 *)op_buf(k, next), k->N, k->R, n, wscale, kc, kh,
-        sc, k->seed);
+    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(
+        k->P, k->theta, k->theta_t, k->g1, k->psi, omega, (__nv_bfloat16 *)op_buf(k, next), k->N, n, wscale, kc,
+        kh, sc, k->seed);
   else
-    kg_stage_kernel<STAGE, float><<<grid, 256, 0, s>>>(k->P, k->theta, k->theta_t, k->g1, omega,
-                                                       (float *)op_buf(k, next), k->N, k->R, n, wscale, kc, kh,
-                                                       sc, k->seed);
+    kg_stage_kernel<STAGE, float><<<grid_nr(k), 256, 0, s>>>(k->P, k->theta, k->theta_t, k->g1, k->psi, omega,
+                                                             (float *)op_buf(k, next), k->N, n, wscale, kc, kh,
+                                                             sc, k->seed);
   return cudaGetLastError();
 }
 
@@ -318,6 +312,7 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
   if ((e = cudaMalloc((void **)&k->theta_t, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = cudaMalloc((void **)&k->g1, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = cudaMalloc((void **)&k->P, NR * 2 * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void **)&k->psi, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if (is_tc(k)) {
     if ((e = cudaMalloc((void **)&k->Kbf16, NN * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc((void **)&k->Bt, NR * 2 * 2 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -351,6 +346,7 @@ void kuramoto_general_free(KuramotoCtx *k) {
   cudaFree(k->Bt);
   cudaFree(k->Bt32);
   cudaFree(k->P);
+  cudaFree(k->psi);
   delete (GemmPlan *)k->gemm_plan;
   k->gemm_plan = nullptr;
 }
@@ -404,7 +400,7 @@ sde_status kuramoto_general_coupling(KuramotoCtx *k, float *out, cudaStream_t s)
   }
   SDE_CUDA_TRY(launch_operand(k, 0, s));
   SDE_CUDA_TRY(launch_gemm(k, 0, s));
-  kg_coupling_kernel<<<grid_for(k->N * k->R, k->sm_count), 256, 0, s>>>(k->P, k->theta, out, k->N, k->R);
+  kg_coupling_kernel<<<grid_nr(k), 256, 0, s>>>(k->P, k->theta, out, k->N);
   SDE_CUDA_TRY(cudaGetLastError());
   return SDE_OK;
 }

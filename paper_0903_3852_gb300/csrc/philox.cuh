@@ -58,6 +58,17 @@ __device__ __forceinline__ void gauss4(uint32_t g, uint32_t c1, uint32_t c2, uin
   box_muller(r.z, r.w, z[2], z[3]);
 }
 
+// The one Gaussian of step n of a stream, identical to element n & 3 of
+// gauss4 for the block n / 4 (only the Box-Muller pair that holds it is
+// evaluated).
+__device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uint32_t tag, uint2 key) {
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 2), c1, c2, tag), key);
+  const bool hi = (n & 2) != 0;
+  float z0, z1;
+  box_muller(hi ? r.z : r.x, hi ? r.w : r.y, z0, z1);
+  return (n & 1) ? z1 : z0;
+}
+
 // Element k (0..3) of a 4-vector without dynamic register indexing.
 __device__ __forceinline__ float pick4(const float (&z)[4], int k) {
   return k == 0 ? z[0] : (k == 1 ? z[1] : (k == 2 ? z[2] : z[3]));
