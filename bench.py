@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--block", type=int, default=0, help="fixed threads per block (skips autotuning)")
     ap.add_argument("--ilp", type=int, default=0, help="fixed paths per thread (skips autotuning)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fused", action="store_true",
+                    help="general coupling, tensor-core form: SRK2 sub-steps in the GEMM epilogue")
     return ap.parse_args()
 
 
@@ -241,8 +243,9 @@ def run_ours(args, rank, world, device):
         model = sde.SDE_KURAMOTO_GENERAL if tc else sde.SDE_KURAMOTO_GENERAL_FP32
         S = args.general_steps or (w["steps"] if tc else 100)
         N, R = w["n_osc"], w["replicas"]
+        flags = sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_FUSED if args.fused else 0)
         ens = sde.Ensemble.kuramoto(model, N, R, 0.0, w["D"], w["dt"], w["seed"],
-                                    sample_every=w["sample_every"], flags=sde.SDE_FLAG_TIME_KERNELS)
+                                    sample_every=w["sample_every"], flags=flags)
         Kdev = torch.from_numpy(w["Kmat"]).to(device)
         ens.set_coupling(Kdev)
         del Kdev
@@ -266,6 +269,7 @@ def run_ours(args, rank, world, device):
         flop_per_launch = 2.0 * N * (2 * R) * N  # one GEMM K . [sin | cos]
         launches_per_step = 4 * S + S // w["sample_every"] + 4
         cfg = {"workload": "kuramoto_general_%s_N%d_R%d" % ("bf16_tcgen05" if tc else "fp32_cudacore", N, R),
+               "stage": "fused into the GEMM epilogue" if args.fused else "separate kernel",
                "steps_per_bench_step": S, "K0": w["K0"], "D": w["D"], "dt": w["dt"],
                "gemm": "M=%d N=%d K=%d per stage, 2 per step" % (N, 2 * R, N),
                "l2": "K matrix %d MiB streams each GEMM; flushed between steps (256 MiB write)"

@@ -65,6 +65,9 @@ typedef enum sde_schedule {
 #define SDE_FLAG_NO_GRAPH 1u     /* launch kernels directly instead of replaying a graph */
 #define SDE_FLAG_TIME_KERNELS 2u /* Kuramoto pairwise / general: CUDA events around every
                                     launch of the dominant kernel (stage / GEMM) */
+#define SDE_FLAG_FUSED 4u        /* general coupling, tensor-core form: run the SRK2
+                                    sub-steps in the GEMM epilogue instead of as
+                                    separate kernels (same results bit for bit) */
 
 /* One parameter point of Eq. 1. */
 typedef struct sde_jj_point {

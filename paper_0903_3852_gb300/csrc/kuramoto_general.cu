@@ -59,41 +59,17 @@ __global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N) {
   op[(2 * r + 1) * N + i] = to_op<T>(c);
 }
 
-// One SRK2 stage for every (replica, oscillator) from the GEMM output Dt.
-// STAGE 0: predictor theta~ = theta + dt/(2 pi) (omega + g1) + sqrt(2 D dt)/(2 pi) psi
-// STAGE 1: corrector theta' = theta + dt/(2 pi) (omega + (g1 + g2) / 2) + ... psi
-// The step's Gaussian psi is drawn in stage 0 and kept for stage 1.
+// One SRK2 stage for every (replica, oscillator) from the GEMM output Dt
+// (the forms without the fused epilogue): the same per-element update as the
+// tensor-core epilogue (tc::stage_element), the next operand written as T.
 // Grid: (N / 256, R).
 template <int STAGE, typename T>
-__global__ void kg_stage_kernel(const float *__restrict__ Dt, uint32_t *theta, uint32_t *theta_t, float *g1,
-                                float *psi_buf, const float *__restrict__ omega, T *op_next, int64_t N, int64_t n,
-                                float wscale, float kc, float kh, float sc, uint64_t seed) {
+__global__ void kg_stage_kernel(const float *__restrict__ Dt, const tc::StageArgs a, T *op_next) {
   const int64_t r = blockIdx.y;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int64_t idx = r * N + i;
-  const uint32_t th_i = STAGE == 0 ? theta[idx] : theta_t[idx];
-  float s, c;
-  sincospif(2.0f * signed_turns(th_i), &s, &c);
-  const float g = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
-  const float wdt = omega[idx] * wscale;
-  uint32_t out;
-  if (STAGE == 0) {
-    const float psi = gauss1(n, (uint32_t)i, (uint32_t)r, kTagKuramoto, seed_to_key(seed));
-    psi_buf[idx] = psi;
-    const float d1 = fmaf(sc, psi, fmaf(kc, g, wdt));
-    out = theta[idx] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
-    theta_t[idx] = out;
-    g1[idx] = g;
-  } else {
-    const float d = fmaf(sc, psi_buf[idx], fmaf(kh, g1[idx] + g, wdt));
-    out = theta[idx] + (uint32_t)__float2int_rn(d * 4294967296.0f);
-    theta[idx] = out;
-  }
-  float so, co;
-  sincospif(2.0f * signed_turns(out), &so, &co);
-  op_next[(2 * r) * N + i] = to_op<T>(so);
-  op_next[(2 * r + 1) * N + i] = to_op<T>(co);
+  if (i >= a.N) return;
+  tc::stage_element<STAGE>(a, op_next, r, i, Dt[(2 * r) * a.N + i], Dt[(2 * r + 1) * a.N + i],
+                           seed_to_key(a.seed));
 }
 
 // Coupling sums alone: out[r][i] = cos x_i Dt[2r][i] - sin x_i Dt[2r+1][i].
@@ -244,18 +220,52 @@ void *op_buf(KuramotoCtx *k, int which) {
   return (void *)(k->Bt32 + (size_t)which * 2 * k->R * k->N);
 }
 
-cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s) {
+tc::StageArgs stage_args(KuramotoCtx *k, int next, const float *omega, int64_t n, int64_t run_begin) {
+  const double inv2pi = 0.15915494309189533577;
+  tc::StageArgs a{};
+  a.theta = k->theta;
+  a.theta_t = k->theta_t;
+  a.g1 = k->g1;
+  a.psi4 = k->psi4;
+  a.omega = omega;
+  a.op_next = (next >= 0 && is_tc(k)) ? (__nv_bfloat16 *)op_buf(k, next) : nullptr;
+  a.N = k->N;
+  a.NR = k->N * k->R;
+  a.n = n;
+  a.fresh = ((n & 3) == 0 || n == run_begin) ? 1 : 0;
+  a.wscale = (float)(k->dt * inv2pi);
+  a.kc = (float)(k->dt * inv2pi);
+  a.kh = (float)(0.5 * k->dt * inv2pi);
+  a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
+  a.seed = k->seed;
+  return a;
+}
+
+template <int BN, int EPI>
+void launch_tc(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
+  GemmPlan *g = (GemmPlan *)k->gemm_plan;
+  const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
+  dim3 grid(M / tc::BM, Ncols / BN);
+  tc::tc_gemm_bf16_kernel<BN, EPI><<<grid, tc::EpiThreads<EPI>::value, tc::Shape<BN>::SMEM_BYTES, s>>>(
+      g->mapK, g->mapOp[which], k->P, M, Kdim, k->err, sa);
+}
+
+// GEMM reading operand buffer `which`; epi = EPI_STORE_D writes Dt, the stage
+// epilogues apply the SRK2 sub-step and write operand buffer 1 - which.
+cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s, int epi = tc::EPI_STORE_D,
+                        const float *omega = nullptr, int64_t n = 0, int64_t run_begin = 0) {
   const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
   if (is_tc(k)) {
     GemmPlan *g = (GemmPlan *)k->gemm_plan;
+    const tc::StageArgs sa = stage_args(k, epi == tc::EPI_STORE_D ? -1 : 1 - which, omega, n, run_begin);
     if (g->bn == 256) {
-      dim3 grid(M / tc::BM, Ncols / 256);
-      tc::tc_gemm_bf16_kernel<256><<<grid, tc::THREADS, tc::Shape<256>::SMEM_BYTES, s>>>(
-          g->mapK, g->mapOp[which], k->P, M, Kdim, k->err);
+      if (epi == tc::EPI_STAGE0) launch_tc<256, tc::EPI_STAGE0>(k, which, sa, s);
+      else if (epi == tc::EPI_STAGE1) launch_tc<256, tc::EPI_STAGE1>(k, which, sa, s);
+      else launch_tc<256, tc::EPI_STORE_D>(k, which, sa, s);
     } else {
-      dim3 grid(M / tc::BM, Ncols / 128);
-      tc::tc_gemm_bf16_kernel<128><<<grid, tc::THREADS, tc::Shape<128>::SMEM_BYTES, s>>>(
-          g->mapK, g->mapOp[which], k->P, M, Kdim, k->err);
+      if (epi == tc::EPI_STAGE0) launch_tc<128, tc::EPI_STAGE0>(k, which, sa, s);
+      else if (epi == tc::EPI_STAGE1) launch_tc<128, tc::EPI_STAGE1>(k, which, sa, s);
+      else launch_tc<128, tc::EPI_STORE_D>(k, which, sa, s);
     }
   } else {
     dim3 grid((M + SG_BM - 1) / SG_BM, (Ncols + SG_BN - 1) / SG_BN);
@@ -268,27 +278,21 @@ dim3 grid_nr(const KuramotoCtx *k) { return dim3((unsigned)((k->N + 255) / 256),
 
 cudaError_t launch_operand(KuramotoCtx *k, int which, cudaStream_t s) {
   if (is_tc(k))
-    kg_operand_kernel<__nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(k->theta, (__nv_bfloat16 *)op_buf(k, which), k->N);
+    kg_operand_kernel<__nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(k->theta, (__nv_bfloat16 *)op_buf(k, which),
+                                                                 k->N);
   else
     kg_operand_kernel<float><<<grid_nr(k), 256, 0, s>>>(k->theta, (float *)op_buf(k, which), k->N);
   return cudaGetLastError();
 }
 
 template <int STAGE>
-cudaError_t launch_stage(KuramotoCtx *k, int next, const float *omega, int64_t n, cudaStream_t s) {
-  const double inv2pi = 0.15915494309189533577;
-  const float wscale = (float)(k->dt * inv2pi);
-  const float kc = (float)(k->dt * inv2pi);
-  const float kh = (float)(0.5 * k->dt * inv2pi);
-  const float sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
+cudaError_t launch_stage(KuramotoCtx *k, int next, const float *omega, int64_t n, int64_t run_begin,
+                         cudaStream_t s) {
+  const tc::StageArgs a = stage_args(k, next, omega, n, run_begin);
   if (is_tc(k))
-    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(
-        k->P, k->theta, k->theta_t, k->g1, k->psi, omega, (__nv_bfloat16 *)op_buf(k, next), k->N, n, wscale, kc,
-        kh, sc, k->seed);
+    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(k->P, a, (__nv_bfloat16 *)op_buf(k, next));
   else
-    kg_stage_kernel<STAGE, float><<<grid_nr(k), 256, 0, s>>>(k->P, k->theta, k->theta_t, k->g1, k->psi, omega,
-                                                             (float *)op_buf(k, next), k->N, n, wscale, kc, kh,
-                                                             sc, k->seed);
+    kg_stage_kernel<STAGE, float><<<grid_nr(k), 256, 0, s>>>(k->P, a, (float *)op_buf(k, next));
   return cudaGetLastError();
 }
 
@@ -312,7 +316,7 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
   if ((e = cudaMalloc((void **)&k->theta_t, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = cudaMalloc((void **)&k->g1, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = cudaMalloc((void **)&k->P, NR * 2 * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  if ((e = cudaMalloc((void **)&k->psi, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = cudaMalloc((void **)&k->psi4, NR * 4 * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if (is_tc(k)) {
     if ((e = cudaMalloc((void **)&k->Kbf16, NN * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc((void **)&k->Bt, NR * 2 * 2 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -325,12 +329,18 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
       st = make_map(&g->mapOp[w], op_buf(k, w), 2 * k->R, k->N, g->bn);
       if (st != SDE_OK) return st;
     }
-    if ((e = cudaFuncSetAttribute(tc::tc_gemm_bf16_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::Shape<256>::SMEM_BYTES)) != cudaSuccess)
-      return cuda_fail(e, "cudaFuncSetAttribute");
-    if ((e = cudaFuncSetAttribute(tc::tc_gemm_bf16_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::Shape<128>::SMEM_BYTES)) != cudaSuccess)
-      return cuda_fail(e, "cudaFuncSetAttribute");
+    const void *kernels[] = {
+        (const void *)tc::tc_gemm_bf16_kernel<256, tc::EPI_STORE_D>,
+        (const void *)tc::tc_gemm_bf16_kernel<256, tc::EPI_STAGE0>,
+        (const void *)tc::tc_gemm_bf16_kernel<256, tc::EPI_STAGE1>,
+        (const void *)tc::tc_gemm_bf16_kernel<128, tc::EPI_STORE_D>,
+        (const void *)tc::tc_gemm_bf16_kernel<128, tc::EPI_STAGE0>,
+        (const void *)tc::tc_gemm_bf16_kernel<128, tc::EPI_STAGE1>};
+    for (int q = 0; q < 6; ++q)
+      if ((e = cudaFuncSetAttribute(kernels[q], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    q < 3 ? tc::Shape<256>::SMEM_BYTES : tc::Shape<128>::SMEM_BYTES)) !=
+          cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute");
   } else {
     if ((e = cudaMalloc((void **)&k->Kf32, NN * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = cudaMalloc((void **)&k->Bt32, NR * 2 * 4 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -346,7 +356,7 @@ void kuramoto_general_free(KuramotoCtx *k) {
   cudaFree(k->Bt);
   cudaFree(k->Bt32);
   cudaFree(k->P);
-  cudaFree(k->psi);
+  cudaFree(k->psi4);
   delete (GemmPlan *)k->gemm_plan;
   k->gemm_plan = nullptr;
 }
@@ -380,14 +390,24 @@ sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStrea
       SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
       ++sample;
     }
+    if (is_tc(k) && (k->flags & SDE_FLAG_FUSED)) {
+      // the SRK2 sub-steps run in the GEMM epilogues
+      SDE_CUDA_TRY(ktime_begin(k, s));
+      SDE_CUDA_TRY(launch_gemm(k, 0, s, tc::EPI_STAGE0, r->omega_dev, n, r->n_begin));
+      SDE_CUDA_TRY(ktime_end(k, s));
+      SDE_CUDA_TRY(ktime_begin(k, s));
+      SDE_CUDA_TRY(launch_gemm(k, 1, s, tc::EPI_STAGE1, r->omega_dev, n, r->n_begin));
+      SDE_CUDA_TRY(ktime_end(k, s));
+      continue;
+    }
     SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 0, s));
     SDE_CUDA_TRY(ktime_end(k, s));
-    SDE_CUDA_TRY(launch_stage<0>(k, 1, r->omega_dev, n, s));
+    SDE_CUDA_TRY(launch_stage<0>(k, 1, r->omega_dev, n, r->n_begin, s));
     SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 1, s));
     SDE_CUDA_TRY(ktime_end(k, s));
-    SDE_CUDA_TRY(launch_stage<1>(k, 0, r->omega_dev, n, s));
+    SDE_CUDA_TRY(launch_stage<1>(k, 0, r->omega_dev, n, r->n_begin, s));
   }
   if (k->M > 0) SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
   return SDE_OK;

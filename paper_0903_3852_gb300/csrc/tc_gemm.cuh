@@ -11,9 +11,10 @@
 //                        STAGES-deep ring of (A, B) tiles guarded by mbarriers
 //   warp 1, one thread : tcgen05.mma issuer (M = 128, N = BN, K = 16 per MMA),
 //                        tcgen05.commit frees a ring slot / signals the end
-//   all 8 warps        : epilogue, tcgen05.ld 32x32b of their TMEM lane
-//                        quarter, stores of Dt (each warp store is one 128 B
-//                        row segment: the TMEM lane is the row index i)
+//   all warps          : epilogue, tcgen05.ld 32x32b of their TMEM lane
+//                        quarter, then either stores of Dt (each warp store
+//                        is one 128 B row segment: the TMEM lane is the row
+//                        index i) or the fused SRK2 sub-step (16 warps)
 // Every mbarrier wait is bounded (about one second of %globaltimer); on expiry
 // the CTA records SDE kErrTimeout, drains its own TMA loads and MMAs with
 // bounded waits, frees its tensor memory and returns.
@@ -24,6 +25,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace sde {
 namespace tc {
@@ -156,13 +158,91 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// D = A * B^T over K = Kdim; Dt is written transposed ([col][row], rows
-// contiguous) so that each column of the tile is one coalesced run.
+// Fused SRK2 sub-step of Eq. 2 in the epilogue (EPI_STAGE0 / EPI_STAGE1):
+// the tile's column pairs (2r, 2r+1) are P_s, P_c of replica r for the row's
+// oscillator i, so g = cos x_i P_s - sin x_i P_c is the coupling sum.
+struct StageArgs {
+  uint32_t *theta;     // [R][N] fixed-point turns
+  uint32_t *theta_t;   // [R][N] predictor phases
+  float *g1;           // [R][N] first-stage coupling sums
+  float *psi4;         // [4][R][N] Gaussians of the current 4-step Philox block, one plane per step
+  const float *omega;  // [R][N]
+  __nv_bfloat16 *op_next;  // [2R][N] operand of the next GEMM (the buffer this GEMM does not read)
+  int64_t N;
+  int64_t NR;     // N * R: plane stride of psi4
+  int64_t n;      // step index
+  int32_t fresh;  // stage 0: draw the Philox block of step n (n % 4 == 0 or first step of a run)
+  float wscale, kc, kh, sc;
+  uint64_t seed;
+};
+
+enum { EPI_STORE_D = 0, EPI_STAGE0 = 1, EPI_STAGE1 = 2 };
+
+__device__ __forceinline__ float signed_turns_tc(uint32_t th) { return (float)(int32_t)th * 2.3283064365386963e-10f; }
+
+// One element of a stage: oscillator i of replica r with coupling
+// components ps = (K sin x)_i, pc = (K cos x)_i.  The Gaussians of a 4-step
+// Philox block are drawn once (stage 0 of its first step in the run) and kept
+// in four planes.  Shared by the fused epilogues and the separate stage
+// kernels, so both give bit-identical phases.
+__device__ __forceinline__ void store_operand(__nv_bfloat16 *op, int64_t idx, float v) {
+  op[idx] = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ void store_operand(float *op, int64_t idx, float v) { op[idx] = v; }
+
+template <int STAGE, typename T>
+__device__ __forceinline__ void stage_element(const StageArgs &a, T *op_next, int64_t r, int64_t i, float ps,
+                                              float pc, uint2 key) {
+  const int64_t idx = r * a.N + i;
+  const uint32_t th_i = STAGE == 0 ? a.theta[idx] : a.theta_t[idx];
+  float s, c;
+  sincospif(2.0f * signed_turns_tc(th_i), &s, &c);
+  const float g = c * ps - s * pc;
+  const float wdt = a.omega[idx] * a.wscale;
+  const int q = (int)(a.n & 3);
+  float psi;
+  if (STAGE == 0 && a.fresh) {
+    float zz[4];
+    gauss4((uint32_t)(a.n >> 2), (uint32_t)i, (uint32_t)r, kTagKuramoto, key, zz);
+    for (int k = q; k < 4; ++k) a.psi4[k * a.NR + idx] = zz[k];
+    psi = pick4(zz, q);
+  } else {
+    psi = a.psi4[q * a.NR + idx];
+  }
+
+  uint32_t out;
+  if (STAGE == 0) {
+    const float d1 = fmaf(a.sc, psi, fmaf(a.kc, g, wdt));
+    out = a.theta[idx] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+    a.theta_t[idx] = out;
+    a.g1[idx] = g;
+  } else {
+    const float d = fmaf(a.sc, psi, fmaf(a.kh, a.g1[idx] + g, wdt));
+    out = a.theta[idx] + (uint32_t)__float2int_rn(d * 4294967296.0f);
+    a.theta[idx] = out;
+  }
+  float so, co;
+  sincospif(2.0f * signed_turns_tc(out), &so, &co);
+  store_operand(op_next, (2 * r) * a.N + i, so);
+  store_operand(op_next, (2 * r + 1) * a.N + i, co);
+}
+
+// D = A * B^T over K = Kdim.  EPI_STORE_D writes Dt transposed ([col][row],
+// rows contiguous) so that each column of the tile is one coalesced run;
+// the stage epilogues apply the SRK2 sub-step instead.
 // Requires M % 128 == 0, Ncols % BN == 0, Kdim % 64 == 0 (checked by the host).
-template <int BN>
-__global__ void __launch_bounds__(THREADS, 1)
+// Threads per CTA: 8 warps for the plain store, 16 for the fused stages
+// (more warps to hide the latency of the per-element SRK2 arithmetic).
+template <int EPI>
+struct EpiThreads {
+  static constexpr int value = EPI == EPI_STORE_D ? 256 : 512;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
     tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                        float *__restrict__ Dt, int M, int Kdim, uint32_t *err) {
+                        float *__restrict__ Dt, int M, int Kdim, uint32_t *err, const StageArgs sa) {
+  constexpr int NGROUPS = EpiThreads<EPI>::value / 128;  // column groups of the epilogue
   using S = Shape<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -245,16 +325,24 @@ __global__ void __launch_bounds__(THREADS, 1)
   const bool ok = mbar_wait(&acc_bar, 0, &no_abort) && !abort_flag;
   tmem_fence_after();
   if (ok) {
-    const int q = warp & 3;      // TMEM lane quarter this warp may access
-    const int half = warp >> 2;  // which half of the BN columns
+    const int q = warp & 3;       // TMEM lane quarter this warp may access
+    const int group = warp >> 2;  // which BN / NGROUPS columns
     const int row = m0 + q * 32 + lane;
+    const uint2 key = seed_to_key(sa.seed);
 #pragma unroll 1
-    for (int cc = 0; cc < BN / 2; cc += 32) {
-      const int col = half * (BN / 2) + cc;
+    for (int cc = 0; cc < BN / NGROUPS; cc += 32) {
+      const int col = group * (BN / NGROUPS) + cc;
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
+      if (EPI == EPI_STORE_D) {
 #pragma unroll
-      for (int i = 0; i < 32; ++i) Dt[(size_t)(n0 + col + i) * (size_t)M + row] = v[i];
+        for (int i = 0; i < 32; ++i) Dt[(size_t)(n0 + col + i) * (size_t)M + row] = v[i];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          stage_element<EPI == EPI_STAGE0 ? 0 : 1>(sa, sa.op_next, (int64_t)((n0 + col) / 2 + j), (int64_t)row,
+                                                   v[2 * j], v[2 * j + 1], key);
+      }
     }
   }
   tmem_fence_before();

@@ -28,6 +28,7 @@ SDE_SCHED_PLAIN = 1
 
 SDE_FLAG_NO_GRAPH = 1
 SDE_FLAG_TIME_KERNELS = 2
+SDE_FLAG_FUSED = 4
 
 
 class SDEError(RuntimeError):
