@@ -199,7 +199,7 @@ def run_ours(args, rank, world, device):
                "points": len(w["points"]), "total_paths": n, "path_steps": units,
                "steps_per_period": w["steps_per_period"],
                "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
-               "tuning": dict(zip(("block_threads", "paths_per_thread"), ens.tuning())),
+               "tuning": dict(zip(("block_threads", "paths_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write); state 9 MB, compute-bound"}
     elif args.workload in ("kuramoto-meanfield", "kuramoto-pairwise"):
         w = inputs.kuramoto_uniform(seed=rank)
@@ -236,6 +236,7 @@ def run_ours(args, rank, world, device):
             flop_per_launch = flop_per_unit * w["n_osc"] ** 2 * w["replicas"]  # one stage launch
         cfg = {"workload": "kuramoto_%s_N%d_R%d" % (args.workload.split("-")[1], w["n_osc"], w["replicas"]),
                "steps_per_bench_step": S, "K": w["K"], "D": w["D"], "dt": w["dt"],
+               "tuning": dict(zip(("block_threads", "oscillators_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write)"}
     else:
         w = inputs.kuramoto_general(seed=rank)

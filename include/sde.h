@@ -107,6 +107,9 @@ typedef struct sde_config {
   int32_t block_threads;    /* threads per block; 0 = autotune               */
   int32_t paths_per_thread; /* Josephson paths per thread (1 or 2); 0 = autotune */
   uint32_t flags;           /* SDE_FLAG_*                                     */
+  int32_t cluster_ctas;     /* Kuramoto mean field: CTAs per replica (1, 2 or 4,
+                               a thread-block cluster for 2 and 4); 0 = autotune
+                               together with block_threads                     */
 } sde_config;
 
 /*
@@ -192,9 +195,12 @@ void sde_destroy(sde_ctx *ctx);
 /* Message of the last failed call on this thread ("" if none). */
 const char *sde_last_error(void);
 
-/* Launch shape chosen at create (after autotuning). */
-sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads,
-                          int32_t *paths_per_thread);
+/* Launch shape chosen at create (after autotuning): threads per block, paths
+   (Josephson; values 11 and 12 mean 1 and 2 with registers capped at 64) or
+   oscillators (Kuramoto) per thread, and CTAs per replica (the thread-block
+   cluster of the mean-field kernel; 1 otherwise).  Any pointer may be NULL. */
+sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads, int32_t *per_thread,
+                          int32_t *cluster_ctas);
 
 /*
  * Device time of the dominant kernel of the last run, from CUDA events

@@ -510,15 +510,16 @@ sde_status sde_observables(sde_ctx *c, sde_obs_row *rows, int64_t capacity, int6
 
 void sde_destroy(sde_ctx *c) { free_ctx(c); }
 
-sde_status sde_get_tuning(const sde_ctx *c, int32_t *block, int32_t *ilp) {
+sde_status sde_get_tuning(const sde_ctx *c, int32_t *block, int32_t *ilp, int32_t *cluster) {
   clear_error();
   SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
   if (c->kur) {
-    kuramoto_tuning(c->kur, block, ilp);
+    kuramoto_tuning(c->kur, block, ilp, cluster);
     return SDE_OK;
   }
   if (block) *block = c->block;
   if (ilp) *ilp = c->ilp;
+  if (cluster) *cluster = 1;
   return SDE_OK;
 }
 

@@ -26,6 +26,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "kuramoto.h"
 #include "kuramoto_internal.h"
 #include "philox.cuh"
@@ -157,6 +159,130 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
     const int64_t i = threadIdx.x + (int64_t)k * blockDim.x;
     if (valid[k]) A.theta_out[base + i] = th[k];
   }
+}
+
+// Mean field with one replica spread over a thread-block cluster of CS CTAs
+// (CS from the launch): each CTA holds N / CS oscillators in registers and
+// reduces its partial (S, C); the partials are exchanged through distributed
+// shared memory after one cluster barrier per stage (slots double-buffered
+// across stages), and every CTA adds them in the same order, so all CTAs of
+// a replica use identical sums.
+template <int OPT>
+__global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const KurArgs A) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ float2 red[2][32];
+  __shared__ float2 xch[2];
+  const int cs = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int rep = blockIdx.x / cs;
+  const int64_t N = A.N;
+  const int64_t chunk = (N + cs - 1) / cs;
+  const int64_t i0 = (int64_t)crank * chunk;
+  const int64_t base = (int64_t)rep * N;
+  const uint2 key = seed_to_key(A.seed);
+  uint32_t th[OPT];
+  float wdt[OPT];
+  bool valid[OPT];
+  uint32_t oid[OPT];
+#pragma unroll
+  for (int k = 0; k < OPT; ++k) {
+    const int64_t li = threadIdx.x + (int64_t)k * blockDim.x;
+    const int64_t i = i0 + li;
+    valid[k] = li < chunk && i < N;
+    oid[k] = (uint32_t)i;
+    th[k] = valid[k] ? A.theta_in[base + i] : 0u;
+    wdt[k] = valid[k] ? A.omega[base + i] * A.wscale : 0.0f;
+  }
+  int slot = 0, xslot = 0;
+  int64_t sample_ctr = 0, sample_idx = 0;
+  // cluster-wide (S, C): block partial -> DSMEM exchange -> fixed-order sum
+  auto cluster_sum = [&](float S, float C) -> float2 {
+    const float2 part = block_sum2(S, C, red[slot]);
+    slot ^= 1;
+    if (threadIdx.x == 0) xch[xslot] = part;
+    cluster.sync();
+    float2 tot = make_float2(0.0f, 0.0f);
+    for (int q = 0; q < cs; ++q) {
+      const float2 v = *cluster.map_shared_rank(&xch[xslot], q);
+      tot.x += v.x;
+      tot.y += v.y;
+    }
+    xslot ^= 1;
+    return tot;
+  };
+  for (int64_t n = A.n_begin; n < A.n_end;) {
+    const int64_t g = n >> 2;
+    float z[OPT][4];
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) gauss4((uint32_t)g, oid[k], (uint32_t)rep, kTagKuramoto, key, z[k]);
+    const int s0 = (int)(n & 3);
+    const int64_t rem = A.n_end - (g << 2);
+    const int s1 = rem < 4 ? (int)rem : 4;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (s < s0 || s >= s1) continue;
+      float sn[OPT], cs_[OPT], t[OPT];
+      float S = 0.0f, C = 0.0f;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        t[k] = (float)(int32_t)th[k] * 2.3283064365386963e-10f;
+        sincospif(2.0f * t[k], &sn[k], &cs_[k]);
+        if (!valid[k]) sn[k] = cs_[k] = 0.0f;
+        S += sn[k];
+        C += cs_[k];
+      }
+      float2 sc = cluster_sum(S, C);
+      if (A.M > 0 && sample_ctr == 0) {
+        if (threadIdx.x == 0 && crank == 0 && A.r_out) {
+          const double Sd = sc.x, Cd = sc.y;
+          A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+        }
+        ++sample_idx;
+      }
+      if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
+      float g1[OPT], sn2[OPT], cs2[OPT];
+      float S2 = 0.0f, C2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
+        const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
+        sincospif(2.0f * (t[k] + d1), &sn2[k], &cs2[k]);
+        if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
+        S2 += sn2[k];
+        C2 += cs2[k];
+      }
+      sc = cluster_sum(S2, C2);
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        const float g2 = cs2[k] * sc.x - sn2[k] * sc.y;
+        const float d = fmaf(A.sc, z[k][s], fmaf(A.kh, g1[k] + g2, wdt[k]));
+        th[k] += (uint32_t)__float2int_rn(d * 4294967296.0f);
+      }
+    }
+    n = (g + 1) << 2;
+  }
+  if (A.M > 0) {
+    float S = 0.0f, C = 0.0f;
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) {
+      float sn, c;
+      sincospif(2.0f * ((float)(int32_t)th[k] * 2.3283064365386963e-10f), &sn, &c);
+      if (valid[k]) {
+        S += sn;
+        C += c;
+      }
+    }
+    const float2 sc = cluster_sum(S, C);
+    if (threadIdx.x == 0 && crank == 0 && A.r_out) {
+      const double Sd = sc.x, Cd = sc.y;
+      A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < OPT; ++k)
+    if (valid[k]) A.theta_out[base + oid[k]] = th[k];
+  cluster.sync();  // no CTA leaves while others may still read its exchange slots
 }
 
 // ---- pairwise form (Alg. 3) --------------------------------------------
@@ -332,7 +458,35 @@ void *mf_kernel_ptr() {
   return (void *)kur_meanfield_kernel<OPT>;
 }
 
-cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, cudaStream_t s) {
+template <int OPT>
+cudaError_t launch_mf_cluster(const KurArgs &a, int block, int cs, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.R * cs));
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kur_meanfield_cluster_kernel<OPT>, a);
+}
+
+// cs > 1: one replica per cluster of cs CTAs (opt oscillators per thread of
+// each CTA); cs == 1: one CTA per replica.
+cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, int cs, cudaStream_t s) {
+  if (cs > 1) {
+    switch (opt) {
+      case 1: return launch_mf_cluster<1>(a, block, cs, s);
+      case 2: return launch_mf_cluster<2>(a, block, cs, s);
+      case 4: return launch_mf_cluster<4>(a, block, cs, s);
+      case 8: return launch_mf_cluster<8>(a, block, cs, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (opt) {
     case 1: kur_meanfield_kernel<1><<<(unsigned)a.R, block, 0, s>>>(a); break;
     case 2: kur_meanfield_kernel<2><<<(unsigned)a.R, block, 0, s>>>(a); break;
@@ -353,6 +507,110 @@ int pow2_at_least(int64_t x) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+
+namespace {
+
+struct MfShape {
+  int cs, block, opt;
+};
+
+// Candidate shapes for the mean-field kernel: one CTA per replica, or a
+// cluster of 2 or 4 CTAs per replica (distributed shared memory reductions).
+std::vector<MfShape> meanfield_candidates(int64_t N) {
+  std::vector<MfShape> out;
+  for (int cs : {1, 2, 4}) {
+    const int64_t chunk = (N + cs - 1) / cs;
+    for (int block : {256, 512, 1024}) {
+      if (cs > 1 && block > 512) continue;
+      if (block > ((chunk + 31) / 32) * 32 && block > 256) continue;  // mostly idle threads
+      const int opt = pow2_at_least((chunk + block - 1) / block);
+      const int max_opt = cs > 1 ? 8 : 16;
+      const int max_block = cs > 1 ? 512 : (opt <= 2 ? 1024 : 512);
+      if (opt > max_opt || block > max_block) continue;
+      out.push_back({cs, block, opt});
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+// Time a short run of every candidate shape on scratch phases and keep the
+// fastest.
+sde_status meanfield_autotune(KuramotoCtx *k, int only_cs) {
+  auto cands = meanfield_candidates(k->N);
+  if (only_cs > 0) {
+    std::vector<MfShape> keep;
+    for (const auto &c : cands)
+      if (c.cs == only_cs) keep.push_back(c);
+    cands.swap(keep);
+  }
+  if (cands.empty()) {
+    set_error("invalid argument: no mean-field launch shape holds n_osc = " + std::to_string(k->N));
+    return SDE_ERR_INVALID_ARG;
+  }
+  const size_t NR = (size_t)k->N * (size_t)k->R;
+  float *omega = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  sde_status st = SDE_OK;
+  cudaError_t e;
+  if ((e = cudaMalloc((void **)&omega, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) st = cuda_fail(e, "stream");
+  if (st == SDE_OK && (e = cudaEventCreate(&e0)) != cudaSuccess) st = cuda_fail(e, "event");
+  if (st == SDE_OK && (e = cudaEventCreate(&e1)) != cudaSuccess) st = cuda_fail(e, "event");
+  if (st == SDE_OK) {
+    cudaMemsetAsync(omega, 0, NR * 4, s);
+    cudaMemsetAsync(k->theta, 0, NR * 4, s);
+    KurArgs a{};
+    a.theta_in = k->theta;
+    a.theta_out = k->theta;
+    a.omega = omega;
+    a.r_out = nullptr;
+    a.N = k->N;
+    a.R = k->R;
+    a.n_begin = 0;
+    a.n_end = 64;
+    a.M = 0;
+    a.wscale = 1e-3f;
+    a.kc = 1e-4f;
+    a.kh = 5e-5f;
+    a.sc = 1e-3f;
+    a.seed = 0;
+    a.err = k->err;
+    float best = 1e30f;
+    for (const MfShape &c : cands) {
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3 && st == SDE_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        if ((e = launch_meanfield(a, c.block, c.opt, c.cs, s)) != cudaSuccess) {
+          st = cuda_fail(e, "mean-field autotune launch");
+          break;
+        }
+        cudaEventRecord(e1, s);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+          st = cuda_fail(e, "mean-field autotune");
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tmin = std::min(tmin, ms);
+      }
+      if (st != SDE_OK) break;
+      if (tmin < best) {
+        best = tmin;
+        k->cs = c.cs;
+        k->block = c.block;
+        k->opt = c.opt;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(omega);
+  return st;
+}
 
 sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, KuramotoCtx **out) {
   *out = nullptr;
@@ -400,12 +658,17 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
     return st;
   }
   // Launch shape.
-  if (cfg->model == SDE_KURAMOTO_MEANFIELD) {
-    int block = cfg->block_threads;
-    if (block == 0) {
-      block = (int)std::min<int64_t>(1024, ((k->N + 31) / 32) * 32);
-      if (k->N > 2048) block = 512;
+  SDE_CHECK_ARG(cfg->cluster_ctas == 0 || cfg->cluster_ctas == 1 || cfg->cluster_ctas == 2 ||
+                    cfg->cluster_ctas == 4,
+                "cluster_ctas must be 0, 1, 2 or 4");
+  if (cfg->model == SDE_KURAMOTO_MEANFIELD && cfg->block_threads == 0) {
+    st = meanfield_autotune(k, cfg->cluster_ctas);
+    if (st != SDE_OK) {
+      kuramoto_destroy(k);
+      return st;
     }
+  } else if (cfg->model == SDE_KURAMOTO_MEANFIELD) {
+    int block = cfg->block_threads;
     int opt = pow2_at_least((k->N + block - 1) / block);
     if (block < 32 || block % 32 != 0 || block > (opt <= 2 ? 1024 : 512) || opt > 16) {
       kuramoto_destroy(k);
@@ -423,9 +686,10 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   return SDE_OK;
 }
 
-void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread) {
+void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread, int32_t *cluster) {
   if (block) *block = k->block;
   if (per_thread) *per_thread = k->opt;
+  if (cluster) *cluster = k->cs;
 }
 
 cudaError_t ktime_begin(KuramotoCtx *k, cudaStream_t s) {
@@ -523,7 +787,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
     a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
     a.seed = k->seed;
     a.err = k->err;
-    SDE_CUDA_TRY(launch_meanfield(a, k->block, k->opt, s));
+    SDE_CUDA_TRY(launch_meanfield(a, k->block, k->opt, k->cs, s));
   } else if (k->model == SDE_KURAMOTO_PAIRWISE) {
     KurPairArgs a{};
     a.theta = k->theta;

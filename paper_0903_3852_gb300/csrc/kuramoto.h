@@ -20,7 +20,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
 sde_status kuramoto_set_coupling(KuramotoCtx *k, const float *K_dev, cudaStream_t s);
 // out[r][i] = sum_j K_ij sin(phi_j - phi_i) through the model's coupling path.
 sde_status kuramoto_coupling(KuramotoCtx *k, const float *phi_dev, float *out_dev, cudaStream_t s);
-void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread);
+void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread, int32_t *cluster);
 // Mean and total device time of the dominant kernel's launches in the last
 // run, when they were timed per launch; false if they were not.
 bool kuramoto_kernel_stats(KuramotoCtx *k, float *mean_ms, float *total_ms, int64_t *launches);

@@ -22,6 +22,7 @@ struct KuramotoCtx {
   uint32_t *err = nullptr;
   uint32_t flags = 0;
   int block = 0, opt = 0;
+  int cs = 1;  // mean field: CTAs per replica (thread-block cluster size)
   // phases as fixed-point turns, [R][N]
   uint32_t *theta = nullptr;
   uint32_t *theta_t = nullptr;  // predictor phases (pairwise, general)

@@ -50,7 +50,7 @@ class Config(ctypes.Structure):
                 ("n_osc", ctypes.c_int64), ("n_replicas", ctypes.c_int64), ("K", ctypes.c_double),
                 ("D", ctypes.c_double), ("dt", ctypes.c_double), ("sample_every", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("paths_per_thread", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("cluster_ctas", ctypes.c_int32)]
 
 
 class RunDesc(ctypes.Structure):
@@ -87,7 +87,7 @@ SIGNATURES = [
     ("sde_destroy", None, [_VP]),
     ("sde_last_error", ctypes.c_char_p, []),
     ("sde_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32),
-                                      ctypes.POINTER(ctypes.c_int32)]),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("sde_last_kernel_ms", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     ("sde_last_kernel_stats", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float),
                                              ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)]),
@@ -206,7 +206,7 @@ class Ensemble:
 
     @classmethod
     def kuramoto(cls, model, n_osc, n_replicas, K, D, dt, seed, sample_every=100, block_threads=0,
-                 flags=0):
+                 flags=0, cluster_ctas=0):
         cfg = Config()
         cfg.model = model
         cfg.seed = seed
@@ -218,6 +218,7 @@ class Ensemble:
         cfg.sample_every = sample_every
         cfg.block_threads = block_threads
         cfg.flags = flags
+        cfg.cluster_ctas = cluster_ctas
         e = cls(cfg)
         e.n_osc, e.n_replicas, e.sample_every = n_osc, n_replicas, sample_every
         return e
@@ -263,9 +264,10 @@ class Ensemble:
         return out.copy()
 
     def tuning(self):
-        b, i = ctypes.c_int32(), ctypes.c_int32()
-        _check(lib().sde_get_tuning(self._h, ctypes.byref(b), ctypes.byref(i)))
-        return b.value, i.value
+        """(threads per block, paths or oscillators per thread, CTAs per replica)."""
+        b, i, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sde_get_tuning(self._h, ctypes.byref(b), ctypes.byref(i), ctypes.byref(c)))
+        return b.value, i.value, c.value
 
     def last_kernel_ms(self):
         ms = ctypes.c_float()

@@ -56,7 +56,7 @@ int main(void) {
   printf("sde_config %zu\nsde_run_desc %zu\nsde_obs_row %zu\nsde_jj_point %zu\n",
          sizeof(sde_config), sizeof(sde_run_desc), sizeof(sde_obs_row), sizeof(sde_jj_point));
   F(sde_config, seed); F(sde_config, points); F(sde_config, n_osc); F(sde_config, dt);
-  F(sde_config, sample_every); F(sde_config, flags);
+  F(sde_config, sample_every); F(sde_config, flags); F(sde_config, cluster_ctas);
   F(sde_run_desc, r_out_dev); F(sde_run_desc, vsum_out_dev);
   return 0;
 }''')
