@@ -162,19 +162,22 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
 }
 
 // Mean field with one replica spread over a thread-block cluster of CS CTAs
-// (CS from the launch): each CTA holds N / CS oscillators in registers and
-// reduces its partial (S, C); the partials are exchanged through distributed
-// shared memory after one cluster barrier per stage (slots double-buffered
-// across stages), and every CTA adds them in the same order, so all CTAs of
-// a replica use identical sums.
+// (CS from the launch): each CTA holds N / CS oscillators in registers.  Per
+// stage every warp reduces its (S, C) with shuffles and stores the pair into
+// its slot of every CTA of the cluster (distributed shared memory); one
+// cluster barrier later each warp of each CTA sums the CS x warps slots in
+// the same fixed order, so all CTAs of a replica use identical sums.  Slots
+// are double-buffered across stages, so one barrier per stage suffices.
 template <int OPT>
 __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const KurArgs A) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ float2 red[2][32];
-  __shared__ float2 xch[2];
+  __shared__ float2 slots[2][32];  // [buffer][cluster rank * warps + warp]
   const int cs = (int)cluster.num_blocks();
   const int crank = (int)cluster.block_rank();
+  const int nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nslots = cs * nwarps;  // <= 32, checked by the host
   const int rep = blockIdx.x / cs;
   const int64_t N = A.N;
   const int64_t chunk = (N + cs - 1) / cs;
@@ -194,22 +197,19 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
     th[k] = valid[k] ? A.theta_in[base + i] : 0u;
     wdt[k] = valid[k] ? A.omega[base + i] * A.wscale : 0.0f;
   }
-  int slot = 0, xslot = 0;
+  int buf = 0;
   int64_t sample_ctr = 0, sample_idx = 0;
-  // cluster-wide (S, C): block partial -> DSMEM exchange -> fixed-order sum
+  // cluster-wide (S, C)
   auto cluster_sum = [&](float S, float C) -> float2 {
-    const float2 part = block_sum2(S, C, red[slot]);
-    slot ^= 1;
-    if (threadIdx.x == 0) xch[xslot] = part;
-    cluster.sync();
-    float2 tot = make_float2(0.0f, 0.0f);
-    for (int q = 0; q < cs; ++q) {
-      const float2 v = *cluster.map_shared_rank(&xch[xslot], q);
-      tot.x += v.x;
-      tot.y += v.y;
+    const float2 part = warp_sum2(S, C);
+    if (lane < cs) {
+      float2 *dst = cluster.map_shared_rank(&slots[buf][crank * nwarps + warp], lane);
+      *dst = part;
     }
-    xslot ^= 1;
-    return tot;
+    cluster.sync();
+    const float2 v = lane < nslots ? slots[buf][lane] : make_float2(0.0f, 0.0f);
+    buf ^= 1;
+    return warp_sum2(v.x, v.y);
   };
   for (int64_t n = A.n_begin; n < A.n_end;) {
     const int64_t g = n >> 2;
@@ -521,7 +521,7 @@ std::vector<MfShape> meanfield_candidates(int64_t N) {
   for (int cs : {1, 2, 4}) {
     const int64_t chunk = (N + cs - 1) / cs;
     for (int block : {256, 512, 1024}) {
-      if (cs > 1 && block > 512) continue;
+      if (cs > 1 && cs * (block / 32) > 32) continue;  // one exchange slot per warp of the cluster
       if (block > ((chunk + 31) / 32) * 32 && block > 256) continue;  // mostly idle threads
       const int opt = pow2_at_least((chunk + block - 1) / block);
       const int max_opt = cs > 1 ? 8 : 16;

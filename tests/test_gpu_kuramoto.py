@@ -29,13 +29,19 @@ def _phase_err(phig, phio):
     return np.abs(angle_diff(phig, phio)) / np.maximum(1.0, np.mod(phio, 2 * np.pi))
 
 
-def _sensitivity(phi0, omega, D, dt, steps, seed, r, Kconst, meanfield):
-    """Growth of a 1e-7 change of every initial phase, per oscillator, in the
-    FP64 oracle itself (oscillators near the edge of locking amplify it)."""
+def _sensitivity(phi0, omega, D, dt, steps, seed, r, Kconst, meanfield, trials=3):
+    """Growth of independent random 1e-7 changes of the initial phases, per
+    oscillator, in the FP64 oracle itself (maximum over a few trials;
+    oscillators near the edge of locking amplify them).  A common shift of all
+    phases would not do: it is a symmetry of Eq. 2."""
+    rng = np.random.default_rng(100 + r)
     a, _ = oracle.kuramoto_run(phi0, omega, D, dt, 0, steps, seed, r, Kconst=Kconst, meanfield=meanfield)
-    b, _ = oracle.kuramoto_run(np.asarray(phi0, np.float64) + 1e-7, omega, D, dt, 0, steps, seed, r,
-                               Kconst=Kconst, meanfield=meanfield)
-    return np.abs(angle_diff(b, a)) / 1e-7
+    G = np.zeros(a.size)
+    for _ in range(trials):
+        b, _ = oracle.kuramoto_run(np.asarray(phi0, np.float64) + 1e-7 * rng.standard_normal(a.size), omega, D,
+                                   dt, 0, steps, seed, r, Kconst=Kconst, meanfield=meanfield)
+        G = np.maximum(G, np.abs(angle_diff(b, a)) / 1e-7)
+    return G
 
 
 @pytest.mark.parametrize("N,R,block,cluster", [(1000, 3, 0, 0), (4096, 2, 0, 0), (4096, 2, 256, 0), (37, 2, 0, 0),
@@ -54,10 +60,11 @@ def test_meanfield_pathwise(N, R, block, cluster):
                                        Kconst=2.0 / N, meanfield=True, sample_every=M)
         err = _phase_err(phig[r], phio)
         G = _sensitivity(w["phi0"][r], w["omega"][r], 0.05, 0.01, steps, seed, r, 2.0 / N, True)
-        # the bar everywhere the oracle itself is insensitive; FP32 rounding
-        # (~1e-7 per step) amplified at most by the oracle's own growth elsewhere
+        # the bar everywhere the oracle itself is insensitive; elsewhere FP32
+        # rounding accumulated over the run (about sqrt(10^3) x 6e-8 = 2e-6)
+        # amplified at most by the oracle's own growth G
         assert err[G <= 30].max(initial=0.0) <= 1e-5
-        assert np.all(err <= 1e-5 + 1e-7 * G)
+        assert np.all(err <= 1e-5 + 2e-6 * G)
         worst = max(worst, err[G <= 30].max(initial=0.0))
         assert np.max(np.abs(rg[:, r] - ro)) <= 2e-5
     print("meanfield N=%d max phase err (insensitive oscillators) %.2e" % (N, worst))
