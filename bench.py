@@ -29,6 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_0903_3852_gb300 import dist as sde_dist  # noqa: E402
 from paper_0903_3852_gb300 import inputs  # noqa: E402
 
 PAPER_FLOP_PER_STEP = 79  # Table 1 (Appendix): FLOP per SRK2 step of Eq. 1, weighted
@@ -119,7 +120,7 @@ class ClockSampler:
 def sweep_workload(rank, args=None):
     w = inputs.josephson_sweep()
     # each rank integrates its own copy with its own noise key (weak scaling)
-    w["seed"] = w["seed"] + 1000 * rank
+    w["seed"] = sde_dist.rank_seed(w["seed"], rank)
     if args is not None and (args.points or args.steps_cap):
         k = args.points or len(w["points"])
         n = int(w["paths"][:k].sum())
@@ -132,7 +133,7 @@ def sweep_workload(rank, args=None):
 
 def plain_workload(rank):
     w = inputs.josephson_plain()
-    w["seed"] = w["seed"] + 1000 * rank
+    w["seed"] = sde_dist.rank_seed(w["seed"], rank)
     return w
 
 
@@ -304,9 +305,7 @@ def run_ours(args, rank, world, device):
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = sde_dist.max_over_ranks(ms, device=torch.device("cuda", device))
         dist.barrier()
 
     # end to end through the public API with host buffers
@@ -334,7 +333,7 @@ def run_ours(args, rank, world, device):
     achieved = flop_per_launch / (k_ms * 1e-3) / 1e12
     res = {
         "metric": metric,
-        "value": units * world / (ms * 1e-3),
+        "value": sde_dist.aggregate_rate(units, world, ms * 1e-3),
         "unit": metric.split("/")[0] + "/s",
         "n_gpus": world,
         "steps": args.steps,
