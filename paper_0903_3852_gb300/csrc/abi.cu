@@ -150,6 +150,7 @@ JJLaunchArgs jj_args(const sde_ctx *c, const sde_run_desc *r, int ilp) {
   a.n_begin = r->n_begin;
   a.n_end = r->n_end;
   a.seed = c->cfg.seed;
+  a.keys = philox_round_keys(c->cfg.seed);
   return a;
 }
 

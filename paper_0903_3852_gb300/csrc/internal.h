@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace sde {
 
@@ -72,6 +73,7 @@ struct JJLaunchArgs {
   JJState st;
   int64_t n_begin, n_end;
   uint64_t seed;
+  PhiloxKeys keys;  // round keys of seed
 };
 
 // Kernel launchers (josephson.cu).

@@ -86,18 +86,19 @@ template <int ILP, bool ACC>
 __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float (&v)[ILP],
                                            double (&vs)[ILP], const JJConsts &c,
                                            const float *__restrict__ drive, int P, int &k,
-                                           int64_t n0, int64_t n1, uint2 key,
+                                           int64_t n0, int64_t n1, const PhiloxKeys &key,
                                            const uint32_t (&pid)[ILP], uint32_t point) {
   if (n0 >= n1) return;
   float acc[ILP];
 #pragma unroll
   for (int i = 0; i < ILP; ++i) acc[i] = 0.0f;
-  const int64_t g0 = n0 >> 2, g1 = (n1 - 1) >> 2;
-  for (int64_t g = g0; g <= g1; ++g) {
+  // group indices fit in 32 bits: steps are at most 2^33
+  const uint32_t g0 = (uint32_t)(n0 >> 2), g1 = (uint32_t)((n1 - 1) >> 2);
+  for (uint32_t g = g0; g <= g1; ++g) {
     float z[ILP][4];
 #pragma unroll
-    for (int i = 0; i < ILP; ++i) gauss4((uint32_t)g, pid[i], point, kTagJosephson, key, z[i]);
-    const int64_t base = g << 2;
+    for (int i = 0; i < ILP; ++i) gauss4(g, pid[i], point, kTagJosephson, key, z[i]);
+    const int64_t base = (int64_t)g << 2;
     if (base >= n0 && base + 4 <= n1) {
       // full group: drive values at t_{4g} .. t_{4g+4}
       float e[5];
@@ -163,7 +164,7 @@ template <int ILP>
 __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, int lane) {
   const JJUnit un = A.units[u];
   const JJConsts c = A.consts[un.point];
-  const uint2 key = seed_to_key(A.seed);
+  const PhiloxKeys &key = A.keys;
   float x[ILP], v[ILP];
   int w[ILP];
   double vs[ILP];
@@ -456,6 +457,7 @@ struct NoallocArgs {
   int64_t steps;
   int64_t n_begin, n_end;
   uint64_t seed;
+  PhiloxKeys keys;
   JJState st;
   Moments *partials;  // device address of g_noalloc_partials
 };
@@ -486,7 +488,7 @@ __global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
   const int n_units = (A.n_paths + 31) / 32;
   if (u >= n_units) return;
   const int lane = threadIdx.x & 31;
-  const uint2 key = seed_to_key(A.seed);
+  const PhiloxKeys &key = A.keys;
   const int j = u * 32 + lane;
   const bool valid = j < A.n_paths;
   float x[1] = {0.0f}, v[1] = {0.0f};
@@ -614,6 +616,7 @@ extern "C" sde_status sde_josephson_run_noalloc(const sde_jj_point *point, int32
   a.n_begin = n_begin;
   a.n_end = n_end;
   a.seed = seed;
+  a.keys = philox_round_keys(seed);
   a.st = JJState{x_in_dev, v_in_dev, w_in_dev, vsum_in_dev, x_out_dev, v_out_dev, w_out_dev, vsum_out_dev};
   a.partials = partials;
   const int n_units = (int)((n_paths + 31) / 32);

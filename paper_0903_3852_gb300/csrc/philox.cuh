@@ -32,6 +32,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// The ten round keys of a seed (k + r W for round r), computed once on the
+// host and passed to kernels as parameters, so that the rounds read them as
+// constant operands.
+struct PhiloxKeys {
+  uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_round_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k[2 * r] = k0;
+    K.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &K) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ K.k[2 * round], lo1, hi0 ^ c.w ^ K.k[2 * round + 1], lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint2 seed_to_key(uint64_t seed) {
   return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }
@@ -43,7 +74,10 @@ __device__ __forceinline__ float uniform24(uint32_t w) {
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1) {
   const float u0 = uniform24(w0);
   const float u1 = uniform24(w1);
-  const float rho = sqrtf(-2.0f * logf(u0));
+  // sqrt(L) as L rsqrt(L) (two instructions, within 2 ulp); L = 0 exactly
+  // when u0 = 1, which 1 in 2^24 draws hit
+  const float L = -2.0f * logf(u0);
+  const float rho = L > 0.0f ? L * rsqrtf(L) : 0.0f;
   float s, c;
   sincospif(2.0f * u1, &s, &c);
   z0 = rho * c;
@@ -54,6 +88,14 @@ __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, 
 __device__ __forceinline__ void gauss4(uint32_t g, uint32_t c1, uint32_t c2, uint32_t tag,
                                        uint2 key, float (&z)[4]) {
   const uint4 r = philox4x32_10(make_uint4(g, c1, c2, tag), key);
+  box_muller(r.x, r.y, z[0], z[1]);
+  box_muller(r.z, r.w, z[2], z[3]);
+}
+
+// gauss4 with precomputed round keys.
+__device__ __forceinline__ void gauss4(uint32_t g, uint32_t c1, uint32_t c2, uint32_t tag,
+                                       const PhiloxKeys &K, float (&z)[4]) {
+  const uint4 r = philox4x32_10(make_uint4(g, c1, c2, tag), K);
   box_muller(r.x, r.y, z[0], z[1]);
   box_muller(r.z, r.w, z[2], z[3]);
 }
