@@ -331,6 +331,12 @@ def run_ours(args, rank, world, device):
     if args.workload in ("sweep", "plain"):
         flop_per_launch = flop_per_unit * units / launches_kernel
     achieved = flop_per_launch / (k_ms * 1e-3) / 1e12
+    # DRAM bytes per launch of the dominant kernel from the ncu captures
+    # summarised under profiles/ (null where the kernel changed since)
+    traffic, traffic_src = None, None
+    if args.workload in ("sweep", "plain"):
+        traffic = 8.7 * n  # jj_kernel: 8.7 B per path (the state read once)
+        traffic_src = "profiles/jj_kernel_sweep_64pts_cap20000.md, scaled by paths"
     res = {
         "metric": metric,
         "value": sde_dist.aggregate_rate(units, world, ms * 1e-3),
@@ -346,7 +352,8 @@ def run_ours(args, rank, world, device):
         "data": "synthetic (seeded; inputs.py)",
         "config": cfg,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "flop_model": flop_note,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "flop_model": flop_note,
                      "peak_source": peak_note, "kernel_ms_per_launch": k_ms},
         "e2e": {"value": units * world / (e2e * 1e-3), "unit": metric.split("/")[0] + "/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
