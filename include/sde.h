@@ -233,6 +233,27 @@ sde_status sde_set_coupling(sde_ctx *ctx, const float *K_dev, void *stream);
 sde_status sde_kuramoto_coupling(sde_ctx *ctx, const float *phi_dev, float *out_dev, void *stream);
 
 /*
+ * Coarse-grained position histogram of a Josephson ensemble (Fig. 2, Sec. 5:
+ * bins exactly one potential period wide): for every point k, counts of the
+ * winding count w (the integer part of the position) of its paths, from the
+ * w array of a run (w_out_dev).  counts_dev[k][0] counts w < w_lo,
+ * counts_dev[k][1 + b] counts w = w_lo + b (b < nbins) and
+ * counts_dev[k][nbins + 1] counts w >= w_lo + nbins.  counts_dev: device,
+ * n_points x (nbins + 2) unsigned 64-bit, overwritten.  nbins in [1, 8192].
+ */
+sde_status sde_position_histogram(sde_ctx *ctx, const int32_t *w_dev, int32_t w_lo, int32_t nbins,
+                                  unsigned long long *counts_dev, void *stream);
+
+/*
+ * Phase density of Kuramoto ensembles (Fig. 4, P(x; t)): counts of n phases
+ * phi_dev (radians, as returned by a run: [0, 2 pi)) in nbins equal bins;
+ * bin = floor(phi * (float)(nbins / 2 pi)) in FP32, clamped to [0, nbins-1].
+ * counts_dev: device, nbins unsigned 64-bit, overwritten.
+ */
+sde_status sde_phase_histogram(const float *phi_dev, int64_t n, int32_t nbins, unsigned long long *counts_dev,
+                               void *stream);
+
+/*
  * Philox4x32-10 (Salmon et al., SC'11; replaces the xorshift generator of
  * Sec. 4.1): out_dev[4i..4i+3] = Philox(counter ctr_dev[4i..4i+3], key =
  * (seed low word, seed high word)).  n counters, n >= 0, device arrays.

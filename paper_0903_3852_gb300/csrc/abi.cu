@@ -43,6 +43,7 @@ struct sde_ctx {
   std::vector<int64_t> paths, steps, offsets;
   JJConsts *consts = nullptr;
   float *drive = nullptr;
+  int64_t *offsets_dev = nullptr, *paths_dev = nullptr;  // per point (histograms)
   JJUnitList units[3];  // indexed by ILP (1, 2)
   Moments *partials = nullptr;
   uint32_t *queue = nullptr;
@@ -82,6 +83,8 @@ void free_ctx(sde_ctx *c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   cudaFree(c->consts);
   cudaFree(c->drive);
+  cudaFree(c->offsets_dev);
+  cudaFree(c->paths_dev);
   for (auto &u : c->units) {
     cudaFree(u.units);
     cudaFree(u.point_range);
@@ -347,8 +350,8 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
   SDE_CUDA_TRY(cudaDeviceSynchronize());
   cudaFree(pts);
   cudaFree(steps);
-  cudaFree(offs);
-  cudaFree(paths);
+  c->offsets_dev = offs;
+  c->paths_dev = paths;
 
   int32_t max_units = 0;
   for (int ilp = 1; ilp <= 2; ++ilp) {
@@ -542,6 +545,32 @@ sde_status sde_last_kernel_ms(sde_ctx *c, float *ms) {
   clear_error();
   SDE_CHECK_ARG(ms != nullptr, "ms is NULL");
   return sde_last_kernel_stats(c, ms, nullptr, nullptr);
+}
+
+sde_status sde_position_histogram(sde_ctx *c, const int32_t *w_dev, int32_t w_lo, int32_t nbins,
+                                  unsigned long long *counts_dev, void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr && c->cfg.model == SDE_JOSEPHSON, "needs a Josephson context");
+  SDE_CHECK_ARG(nbins >= 1 && nbins <= 8192, "nbins must be in [1, 8192]");
+  SDE_CHECK_ARG(counts_dev != nullptr, "counts is NULL");
+  SDE_CHECK_ARG(w_dev != nullptr || c->total_paths == 0, "w is NULL");
+  int64_t max_paths = 0;
+  for (auto p : c->paths) max_paths = std::max(max_paths, p);
+  SDE_CUDA_TRY(winding_hist(w_dev, c->offsets_dev, c->paths_dev, c->n_points, max_paths, w_lo, nbins,
+                            counts_dev, c->sm_count, (cudaStream_t)stream));
+  return SDE_OK;
+}
+
+sde_status sde_phase_histogram(const float *phi_dev, int64_t n, int32_t nbins, unsigned long long *counts_dev,
+                               void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(n >= 0 && nbins >= 1 && nbins <= 8192, "need n >= 0 and nbins in [1, 8192]");
+  SDE_CHECK_ARG(counts_dev != nullptr && (phi_dev != nullptr || n == 0), "phi and counts must be non-NULL");
+  int dev = 0, sms = 0;
+  SDE_CUDA_TRY(cudaGetDevice(&dev));
+  SDE_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SDE_CUDA_TRY(phase_hist(phi_dev, n, nbins, counts_dev, sms, (cudaStream_t)stream));
+  return SDE_OK;
 }
 
 sde_status sde_set_coupling(sde_ctx *c, const float *K_dev, void *stream) {

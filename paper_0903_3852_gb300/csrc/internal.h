@@ -85,6 +85,13 @@ int jj_max_blocks_per_sm(int ilp, int block, int P);
 cudaError_t jj_finalize(const JJConsts *consts, const int2 *point_range, int n_points,
                         const Moments *partials, int64_t n_end, sde_obs_row *obs, cudaStream_t s);
 
+// Histograms (histogram.cu).
+cudaError_t winding_hist(const int32_t *w, const int64_t *offsets, const int64_t *paths, int n_points,
+                         int64_t max_paths, int32_t w_lo, int32_t nbins, unsigned long long *counts,
+                         int sm_count, cudaStream_t s);
+cudaError_t phase_hist(const float *phi, int64_t n, int32_t nbins, unsigned long long *counts, int sm_count,
+                       cudaStream_t s);
+
 cudaError_t philox_fill(const uint32_t *ctr, uint64_t seed, uint32_t *out, int64_t n, cudaStream_t s);
 cudaError_t box_muller_fill(const uint32_t *ctr, uint64_t seed, float *z, int64_t n, cudaStream_t s);
 

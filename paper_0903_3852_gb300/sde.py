@@ -95,6 +95,8 @@ SIGNATURES = [
     ("sde_box_muller", ctypes.c_int, [_VP, ctypes.c_uint64, _VP, ctypes.c_int64, _VP]),
     ("sde_abi_version", ctypes.c_int32, []),
     ("sde_set_coupling", ctypes.c_int, [_VP, _VP, _VP]),
+    ("sde_position_histogram", ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    ("sde_phase_histogram", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
     ("sde_mlp_create", ctypes.c_int, [ctypes.POINTER(MlpConfig), ctypes.POINTER(_VP)]),
     ("sde_mlp_destroy", None, [_VP]),
     ("sde_mlp_num_params", ctypes.c_int64, [_VP]),
@@ -239,6 +241,14 @@ class Ensemble:
         r.phi_in_dev, r.phi_out_dev, r.omega_dev = _ptr(phi_in), _ptr(phi_out), _ptr(omega)
         r.r_out_dev = _ptr(r_out)
         _check(lib().sde_run_ensemble(self._h, ctypes.byref(r), _stream(stream)))
+
+    def position_histogram(self, w, w_lo, nbins, stream=None):
+        """Per-point counts of the winding count w: (n_points, nbins + 2) int64
+        tensor [below, w_lo .. w_lo + nbins - 1, above]."""
+        import torch
+        counts = torch.empty((self.n_points, nbins + 2), dtype=torch.int64, device="cuda")
+        _check(lib().sde_position_histogram(self._h, _ptr(w), w_lo, nbins, _ptr(counts), _stream(stream)))
+        return counts
 
     def set_coupling(self, K, stream=None):
         """K: (N, N) float32 CUDA tensor, row i = receiving oscillator."""
@@ -397,3 +407,11 @@ def points_to_device(points):
     arr = (JJPoint * len(points))(*[JJPoint(p["gamma"], p["a"], p["omega"], p["f"], p["D"]) for p in points])
     buf = bytearray(arr)
     return torch.frombuffer(buf, dtype=torch.uint8).clone().cuda()
+
+
+def phase_histogram(phi, nbins, stream=None):
+    """Counts of the phases phi (radians in [0, 2 pi)) in nbins equal bins."""
+    import torch
+    counts = torch.empty(nbins, dtype=torch.int64, device="cuda")
+    _check(lib().sde_phase_histogram(_ptr(phi), phi.numel(), nbins, _ptr(counts), _stream(stream)))
+    return counts
