@@ -44,10 +44,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise",
-                             "kuramoto-general", "kuramoto-general-fp32", "surrogate"])
+                             "kuramoto-general", "kuramoto-general-fp32", "surrogate", "fig2",
+                             "kuramoto-fig4"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairwise-steps", type=int, default=200,
                     help="steps per bench step of the pairwise Kuramoto workload")
+    ap.add_argument("--fig4-steps", type=int, default=None,
+                    help="kuramoto-fig4: steps per bench step (default: the workload's 2000)")
     ap.add_argument("--general-steps", type=int, default=0,
                     help="steps per bench step of the general-coupling workloads "
                          "(default: all 5000 for BF16, 100 for the FP32 baseline)")
@@ -137,6 +140,12 @@ def plain_workload(rank):
     return w
 
 
+def fig2_workload(rank):
+    w = inputs.josephson_fig2()
+    w["seed"] = sde_dist.rank_seed(w["seed"], rank)
+    return w
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -161,9 +170,10 @@ def run_ours(args, rank, world, device):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
-    if args.workload in ("sweep", "plain"):
-        w = sweep_workload(rank, args) if args.workload == "sweep" else plain_workload(rank)
-        sched = sde.SDE_SCHED_PERSISTENT if args.workload == "sweep" else sde.SDE_SCHED_PLAIN
+    if args.workload in ("sweep", "plain", "fig2"):
+        w = {"sweep": lambda r: sweep_workload(r, args), "plain": plain_workload,
+             "fig2": fig2_workload}[args.workload](rank)
+        sched = sde.SDE_SCHED_PLAIN if args.workload == "plain" else sde.SDE_SCHED_PERSISTENT
         ens = sde.Ensemble.josephson(w["points"], w["paths"], w["steps"], w["seed"],
                                      steps_per_period=w["steps_per_period"], schedule=sched,
                                      block_threads=args.block, paths_per_thread=args.ilp)
@@ -193,7 +203,8 @@ def run_ours(args, rank, world, device):
         launches_kernel = 1  # the timed region brackets the per-step launches as one
         metric = "path-steps/sec"
         flop_per_unit = PAPER_FLOP_PER_STEP
-        name = "josephson_sweep_%dpts" % len(w["points"]) if args.workload == "sweep" else "josephson_plain_1024"
+        name = {"sweep": "josephson_sweep_%dpts" % len(w["points"]), "plain": "josephson_plain_1024",
+                "fig2": "josephson_fig2_524288paths_2e5steps"}[args.workload]
         if args.steps_cap:
             name += "_cap%d" % args.steps_cap
         cfg = {"workload": name,
@@ -202,10 +213,13 @@ def run_ours(args, rank, world, device):
                "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
                "tuning": dict(zip(("block_threads", "paths_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write); state 9 MB, compute-bound"}
-    elif args.workload in ("kuramoto-meanfield", "kuramoto-pairwise"):
-        w = inputs.kuramoto_uniform(seed=rank)
-        model = sde.SDE_KURAMOTO_MEANFIELD if args.workload == "kuramoto-meanfield" else sde.SDE_KURAMOTO_PAIRWISE
+    elif args.workload in ("kuramoto-meanfield", "kuramoto-pairwise", "kuramoto-fig4"):
+        fig4 = args.workload == "kuramoto-fig4"
+        w = inputs.kuramoto_fig4(seed=rank) if fig4 else inputs.kuramoto_uniform(seed=rank)
+        model = sde.SDE_KURAMOTO_PAIRWISE if args.workload == "kuramoto-pairwise" else sde.SDE_KURAMOTO_MEANFIELD
         S = w["steps"] if model == sde.SDE_KURAMOTO_MEANFIELD else args.pairwise_steps
+        if fig4 and args.fig4_steps:
+            S = args.fig4_steps
         ens = sde.Ensemble.kuramoto(model, w["n_osc"], w["replicas"], w["K"], w["D"], w["dt"], w["seed"],
                                     sample_every=w["sample_every"], flags=sde.SDE_FLAG_TIME_KERNELS)
         phi_h = torch.from_numpy(w["phi0"]).pin_memory()
@@ -223,7 +237,12 @@ def run_ours(args, rank, world, device):
 
         h2d = phi_h.numel() * 4
         d2h = 40 * (S // w["sample_every"] + 1)
-        if model == sde.SDE_KURAMOTO_MEANFIELD:
+        if fig4:
+            units = float(w["n_osc"] * w["replicas"] * S)
+            metric = "oscillator-steps/sec"
+            launches_per_step = 2 * S + 4
+            bytes_per_launch = 16.0 * w["n_osc"] * w["replicas"]  # read 8-12 B, write 4-8 B per oscillator
+        elif model == sde.SDE_KURAMOTO_MEANFIELD:
             units = float(w["n_osc"] * w["replicas"] * S)
             metric = "oscillator-steps/sec"
             flop_per_unit = 66  # Appendix: 66 FLOP per step of the mean-field program
@@ -235,7 +254,8 @@ def run_ours(args, rank, world, device):
             flop_per_unit = 6  # Appendix: 44 + 6N FLOP per oscillator-step, 6 per pair term
             launches_per_step = 2 * S + S // w["sample_every"] + 4
             flop_per_launch = flop_per_unit * w["n_osc"] ** 2 * w["replicas"]  # one stage launch
-        cfg = {"workload": "kuramoto_%s_N%d_R%d" % (args.workload.split("-")[1], w["n_osc"], w["replicas"]),
+        cfg = {"workload": "kuramoto_%s_N%d_R%d" % ("fig4_meanfield_grid" if fig4 else args.workload.split("-")[1],
+                                                    w["n_osc"], w["replicas"]),
                "steps_per_bench_step": S, "K": w["K"], "D": w["D"], "dt": w["dt"],
                "tuning": dict(zip(("block_threads", "oscillators_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write)"}
@@ -317,9 +337,31 @@ def run_ours(args, rank, world, device):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = statistics.median(e2e_ms) if e2e_ms else float("nan")
 
+    extra = {}
+    if args.workload == "fig2":
+        # the coarse-grained distribution of Fig. 2 (right): 200 bins, one potential
+        # period each, the window centred on the median winding number
+        w_lo = int(np.median(w_out.cpu().numpy())) - 100
+        counts = ens.position_histogram(w_out, w_lo, 200).cpu().numpy()[0]
+        extra["fig2_histogram"] = {"w_lo": w_lo, "bins": 200, "below": int(counts[0]),
+                                   "above": int(counts[-1]), "counts": [int(c) for c in counts[1:-1]],
+                                   "paper_seconds_c1060_fp32": 20.0}
+    if args.workload == "kuramoto-fig4":
+        # the density P(x; t) of Fig. 4 at the end of the run, and r against
+        # the mean-field self-consistency r = I1(K r / D) / I0(K r / D)
+        nb = 100
+        counts = sde.phase_histogram(phi_out.reshape(-1), nb).cpu().numpy()
+        obs = ens.observables()
+        extra["fig4"] = {"r_end": float(obs["mean"][-1]), "r_theory": 0.8314620247541972,
+                         "histogram_bins": nb, "counts": [int(c) for c in counts],
+                         "paper_seconds_c1060_fp32": 20.0}
     k_ms = statistics.mean(kernel_ms)
     peaks, peak_src = measured_peaks()
-    if args.workload == "kuramoto-general":
+    if args.workload == "kuramoto-fig4":
+        bound, peak = "hbm", peaks["hbm_gbs"]
+        peak_note = "HBM copy bandwidth, %s" % peak_src
+        flop_note = "16 B per oscillator per stage launch (theta, omega or theta~, y read; theta~, y or theta written)"
+    elif args.workload == "kuramoto-general":
         bound, peak = "tensor", peaks["bf16_tflops_sustained"]
         peak_note = "bf16 dense, sustained, %s" % peak_src
         flop_note = "2 N (2R) N FLOP per GEMM launch"
@@ -328,13 +370,16 @@ def run_ours(args, rank, world, device):
         peak_note = "%d SM x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)" % props.multi_processor_count
         flop_note = ("2 N (2R) N FLOP per GEMM launch (FP32 FMA)" if args.workload == "kuramoto-general-fp32"
                      else "%d FLOP per unit (paper Table 1 weighting)" % flop_per_unit)
-    if args.workload in ("sweep", "plain"):
+    if args.workload in ("sweep", "plain", "fig2"):
         flop_per_launch = flop_per_unit * units / launches_kernel
-    achieved = flop_per_launch / (k_ms * 1e-3) / 1e12
+    if args.workload == "kuramoto-fig4":
+        achieved = bytes_per_launch / (k_ms * 1e-3) / 1e9
+    else:
+        achieved = flop_per_launch / (k_ms * 1e-3) / 1e12
     # DRAM bytes per launch of the dominant kernel from the ncu captures
     # summarised under profiles/ (null where the kernel changed since)
     traffic, traffic_src = None, None
-    if args.workload in ("sweep", "plain"):
+    if args.workload in ("sweep", "plain", "fig2"):
         traffic = 8.7 * n  # jj_kernel: 8.7 B per path (the state read once)
         traffic_src = "profiles/jj_kernel_sweep_64pts_cap20000.md, scaled by paths"
     res = {
@@ -351,7 +396,8 @@ def run_ours(args, rank, world, device):
         "dtype": "f32 (FP64 reductions)",
         "data": "synthetic (seeded; inputs.py)",
         "config": cfg,
-        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "flop_model": flop_note,
                      "peak_source": peak_note, "kernel_ms_per_launch": k_ms},
@@ -361,31 +407,36 @@ def run_ours(args, rank, world, device):
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
+    res.update(extra)
     return res, ens
 
 
 def cpu_baseline(args, budget_s=20.0):
     """The FP64 oracle as it stands, on a bounded sample of the workload."""
     import oracle
-    if args.workload in ("sweep", "plain"):
-        w = sweep_workload(0) if args.workload == "sweep" else plain_workload(0)
+    if args.workload in ("sweep", "plain", "fig2"):
+        w = {"sweep": sweep_workload, "plain": plain_workload, "fig2": fig2_workload}[args.workload](0)
         offs = np.concatenate([[0], np.cumsum(w["paths"])])
-        per_point = 2 if args.workload == "sweep" else 64
+        per_point = {"sweep": 2, "plain": 64, "fig2": 256}[args.workload]
         t0 = time.perf_counter()
         done = 0.0
         npts = 0
         for k, pt in enumerate(w["points"]):
             sl = slice(offs[k], offs[k] + min(per_point, int(w["paths"][k])))
             S = int(w["steps"][k])
-            oracle.jj_run(w["x0"][sl], w["v0"][sl], oracle.jj_params(**pt), w["steps_per_period"], 0, S, S,
-                          w["seed"], point=k)
-            done += (sl.stop - sl.start) * S
+            for c in range(sl.start, sl.stop, 16):
+                cs = slice(c, min(c + 16, sl.stop))
+                oracle.jj_run(w["x0"][cs], w["v0"][cs], oracle.jj_params(**pt), w["steps_per_period"], 0, S, S,
+                              w["seed"], point=k, path0=int(c - offs[k]))
+                done += (cs.stop - cs.start) * S
+                if time.perf_counter() - t0 > budget_s:
+                    break
             npts += 1
             if time.perf_counter() - t0 > budget_s:
                 break
         dt = time.perf_counter() - t0
         return {"value": done / dt, "unit": "path-steps/s", "cores": 1, "kind": "oracle",
-                "sample": "first %d paths of each of %d points, full step counts (%.3g path-steps)"
+                "sample": "up to the first %d paths of each of %d points, full step counts (%.3g path-steps)"
                           % (per_point, npts, done)}
     if args.workload.startswith("kuramoto-general"):
         w = inputs.kuramoto_general()
@@ -397,6 +448,15 @@ def cpu_baseline(args, budget_s=20.0):
         return {"value": w["n_osc"] * S / dt, "unit": "oscillator-steps/s", "cores": 1, "kind": "oracle",
                 "sample": "replica 0 of %d, %d step (direct FP64 sum over K_ij, N = %d)"
                           % (w["replicas"], S, w["n_osc"])}
+    if args.workload == "kuramoto-fig4":
+        w = inputs.kuramoto_fig4()
+        S = 2
+        t0 = time.perf_counter()
+        oracle.kuramoto_run(w["phi0"][0], w["omega"][0], w["D"], w["dt"], 0, S, w["seed"], 0,
+                            Kconst=w["K"] / w["n_osc"], meanfield=True)
+        dt = time.perf_counter() - t0
+        return {"value": w["n_osc"] * S / dt, "unit": "oscillator-steps/s", "cores": 1, "kind": "oracle",
+                "sample": "the full replica of %d oscillators, %d steps (mean-field form)" % (w["n_osc"], S)}
     w = inputs.kuramoto_uniform()
     meanfield = args.workload == "kuramoto-meanfield"
     S = 200 if meanfield else 2
@@ -425,8 +485,9 @@ def run_reference(args):
         last = cpu_baseline(args, budget_s=per)
         vals.append(last["value"])
     v = statistics.mean(vals)
-    metric = {"sweep": "path-steps/sec", "plain": "path-steps/sec",
+    metric = {"sweep": "path-steps/sec", "plain": "path-steps/sec", "fig2": "path-steps/sec",
               "kuramoto-meanfield": "oscillator-steps/sec", "kuramoto-pairwise": "pair-terms/sec",
+              "kuramoto-fig4": "oscillator-steps/sec",
               "kuramoto-general": "oscillator-steps/sec",
               "kuramoto-general-fp32": "oscillator-steps/sec"}[args.workload]
     unit = last["unit"]

@@ -53,12 +53,20 @@ typedef enum sde_model {
   SDE_KURAMOTO_GENERAL_FP32 = 4 /* Eq. 2, matrix K_ij: FP32 CUDA-core baseline  */
 } sde_model;
 
-/* Josephson launch schedules. */
+/* Launch schedules.  Josephson: PERSISTENT or PLAIN.  Kuramoto mean field:
+   PERSISTENT picks the form (a replica per CTA or thread-block cluster when
+   n_osc <= 8192, autotuned against the grid-wide form when replicas are
+   few; the grid-wide form above 8192), GRID forces the grid-wide form.  The
+   other Kuramoto models take PERSISTENT (0). */
 typedef enum sde_schedule {
   SDE_SCHED_PERSISTENT = 0, /* all points in one persistent launch with a work
                                queue ordered longest-first, graph-captured   */
-  SDE_SCHED_PLAIN = 1       /* one launch per point, one thread per path
+  SDE_SCHED_PLAIN = 1,      /* one launch per point, one thread per path
                                (the per-path kernel of Alg. 1)               */
+  SDE_SCHED_GRID = 2        /* Kuramoto mean field (Eq. 3) with each replica
+                               spread over the whole grid: two launches per
+                               step, sums reduced by the last block of each
+                               (the form for the 2^24 oscillators of Fig. 4) */
 } sde_schedule;
 
 /* Flags for sde_config.flags. */
@@ -80,7 +88,7 @@ typedef struct sde_jj_point {
 
 typedef struct sde_config {
   int32_t model;    /* sde_model                                             */
-  int32_t schedule; /* sde_schedule (Josephson only)                         */
+  int32_t schedule; /* sde_schedule                                          */
   uint64_t seed;    /* Philox key: (seed & 0xffffffff, seed >> 32)           */
 
   /* ---- Josephson (Eq. 1) -------------------------------------------- */
@@ -198,7 +206,9 @@ const char *sde_last_error(void);
 /* Launch shape chosen at create (after autotuning): threads per block, paths
    (Josephson; values 11 and 12 mean 1 and 2 with registers capped at 64) or
    oscillators (Kuramoto) per thread, and CTAs per replica (the thread-block
-   cluster of the mean-field kernel; 1 otherwise).  Any pointer may be NULL. */
+   cluster of the mean-field kernel; 0 for the grid-wide mean field, whose
+   per-thread count is then the oscillators each thread strides over; 1
+   otherwise).  Any pointer may be NULL. */
 sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads, int32_t *per_thread,
                           int32_t *cluster_ctas);
 

@@ -6,6 +6,11 @@
 //    whole run: its phases stay in registers, S and C come from a block
 //    reduction per stage (two per step), r(t) = sqrt(S^2 + C^2) / N is read
 //    off the first-stage sums.  No grid-wide synchronisation.
+//  * mean field over the whole grid (Eq. 3 for replicas too large for a CTA
+//    or a cluster, such as the 2^24 oscillators of Fig. 4): two launches
+//    per step, each reducing its partial sums of sin/cos through the last
+//    block to finish (fixed-order FP64 sum of the per-block partials, no
+//    waiting between blocks).
 //  * pairwise (Alg. 3 / Fig. 3): the direct all-pairs sum, tiles of source
 //    phases staged in shared memory; one launch per SRK2 stage with the
 //    sub-step fused into the epilogue (Sec. 4.2 splits it into UpdateRHS and
@@ -17,7 +22,8 @@
 // wrap modulo 2 pi is exact integer overflow and the resolution (1.5e-9
 // rad) does not depend on the phase, in the spirit of keeping time modulo
 // the period (Sec. 5).  Drift increments are computed in FP32 and rounded to
-// the fixed-point grid once per step.
+// the fixed-point grid once per stage (the predictor phase too), and sin/cos
+// of a phase come from its fixed-point value directly (turns.cuh).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -31,6 +37,7 @@
 #include "kuramoto.h"
 #include "kuramoto_internal.h"
 #include "philox.cuh"
+#include "turns.cuh"
 
 namespace sde {
 
@@ -93,12 +100,11 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       if (s < s0 || s >= s1) continue;
-      float sn[OPT], cs[OPT], t[OPT];
+      float sn[OPT], cs[OPT];
       float S = 0.0f, C = 0.0f;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
-        t[k] = (float)(int32_t)th[k] * 2.3283064365386963e-10f;  // 2^-32
-        sincospif(2.0f * t[k], &sn[k], &cs[k]);
+        sincos_turns(th[k], sn[k], cs[k]);
         if (!valid[k]) sn[k] = cs[k] = 0.0f;
         S += sn[k];
         C += cs[k];
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
-        sincospif(2.0f * (t[k] + d1), &sn2[k], &cs2[k]);
+        sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
         S2 += sn2[k];
         C2 += cs2[k];
@@ -141,7 +147,7 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
 #pragma unroll
     for (int k = 0; k < OPT; ++k) {
       float sn, cs;
-      sincospif(2.0f * ((float)(int32_t)th[k] * 2.3283064365386963e-10f), &sn, &cs);
+      sincos_turns(th[k], sn, cs);
       if (valid[k]) {
         S += sn;
         C += cs;
@@ -222,12 +228,11 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       if (s < s0 || s >= s1) continue;
-      float sn[OPT], cs_[OPT], t[OPT];
+      float sn[OPT], cs_[OPT];
       float S = 0.0f, C = 0.0f;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
-        t[k] = (float)(int32_t)th[k] * 2.3283064365386963e-10f;
-        sincospif(2.0f * t[k], &sn[k], &cs_[k]);
+        sincos_turns(th[k], sn[k], cs_[k]);
         if (!valid[k]) sn[k] = cs_[k] = 0.0f;
         S += sn[k];
         C += cs_[k];
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
-        sincospif(2.0f * (t[k] + d1), &sn2[k], &cs2[k]);
+        sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
         S2 += sn2[k];
         C2 += cs2[k];
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
 #pragma unroll
     for (int k = 0; k < OPT; ++k) {
       float sn, c;
-      sincospif(2.0f * ((float)(int32_t)th[k] * 2.3283064365386963e-10f), &sn, &c);
+      sincos_turns(th[k], sn, c);
       if (valid[k]) {
         S += sn;
         C += c;
@@ -283,6 +288,164 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
   for (int k = 0; k < OPT; ++k)
     if (valid[k]) A.theta_out[base + oid[k]] = th[k];
   cluster.sync();  // no CTA leaves while others may still read its exchange slots
+}
+
+// ---- mean field over the whole grid ------------------------------------
+
+constexpr int kMfgThreads = 256;
+constexpr int kMfgIlp = 2;  // oscillators per thread per iteration (loads issued together)
+
+struct MfgArgs {
+  uint32_t *theta;    // [R][N] theta_n; the corrector overwrites it with theta_{n+1}
+  uint32_t *theta_t;  // [R][N] predictor phases theta~_n
+  float *y;           // [R][N] first-stage part of the step: wdt + kh g1 + sc psi
+  float *psi;         // [3][R][N] Gaussians of steps 4g+1..4g+3 of the current Philox block
+  const float *omega;
+  float2 *partials;   // [R][gridDim.x] per-block sums
+  double *tot;        // [R][4]: (S, C) of theta_n, then (S, C) of theta~_n
+  uint32_t *count;    // [R] blocks finished in this launch (the last one resets it)
+  double *r_out;      // [rows][R]
+  int64_t N, R;
+  int64_t n;           // step index (noise counter)
+  int64_t sample_row;  // r row written from this launch's totals, -1 = none
+  int32_t gen;         // predictor: draw the Philox block of step n (first step of a block or of a run)
+  float wscale, kc, kh, sc;
+  PhiloxKeys keys;
+};
+
+// MODE 2: sums of (sin, cos) of theta_n.  MODE 0 (predictor): g1 from the
+// totals of theta_n, theta~ = theta + d1, sums over theta~.  MODE 1
+// (corrector): g2 from the totals of theta~, theta_{n+1} = theta + y + kh g2,
+// sums over theta_{n+1} (the next step's first-stage sums).  The Gaussian of
+// step n is element n mod 4 of the Philox block n / 4 of the oscillator (as
+// in the other forms): the predictor draws the block at its first step and
+// keeps the later elements in `psi` for the next three steps.  Each thread
+// strides over the replica; the block's FP32 sums go to `partials`, and the
+// block that finishes last adds all partials of the replica in block order
+// in FP64, so the totals do not depend on which block that is.
+template <int MODE>
+__global__ void __launch_bounds__(kMfgThreads) kur_mfg_kernel(const MfgArgs A) {
+  __shared__ float2 red[32];
+  __shared__ double2 red64[32];
+  __shared__ bool is_last;
+  const int rep = blockIdx.y;
+  const int64_t N = A.N;
+  const int64_t NR = N * A.R;
+  const int64_t base = (int64_t)rep * N;
+  double *tot = A.tot + 4 * rep;
+  float S = 0.0f, C = 0.0f;
+  if (MODE == 0) {
+    S = (float)tot[0];
+    C = (float)tot[1];
+  } else if (MODE == 1) {
+    S = (float)tot[2];
+    C = (float)tot[3];
+  }
+  const int j = (int)(A.n & 3);
+  float ps = 0.0f, pc = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * kMfgThreads * kMfgIlp;
+  for (int64_t i0 = (int64_t)blockIdx.x * kMfgThreads * kMfgIlp + threadIdx.x; i0 < N; i0 += stride) {
+    uint32_t t0[kMfgIlp], tt[kMfgIlp];
+    float a1[kMfgIlp], a2[kMfgIlp];
+    bool ok[kMfgIlp];
+#pragma unroll
+    for (int u = 0; u < kMfgIlp; ++u) {
+      const int64_t i = i0 + u * kMfgThreads;
+      ok[u] = i < N;
+      const int64_t gi = base + (ok[u] ? i : 0);
+      t0[u] = A.theta[gi];
+      if (MODE == 0) {
+        a1[u] = A.omega[gi];
+        a2[u] = A.gen ? 0.0f : A.psi[(int64_t)(j - 1) * NR + gi];
+      } else if (MODE == 1) {
+        tt[u] = A.theta_t[gi];
+        a1[u] = A.y[gi];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kMfgIlp; ++u) {
+      const int64_t i = i0 + u * kMfgThreads;
+      const int64_t gi = base + i;
+      float sn, cs;
+      if (MODE == 2) {
+        sincos_turns(t0[u], sn, cs);
+      } else if (MODE == 0) {
+        float s0, c0;
+        sincos_turns(t0[u], s0, c0);
+        const float g1 = c0 * S - s0 * C;
+        float psi = a2[u];
+        if (A.gen) {
+          float z[4];
+          gauss4((uint32_t)(A.n >> 2), (uint32_t)i, (uint32_t)rep, kTagKuramoto, A.keys, z);
+          psi = pick4(z, j);
+          if (ok[u]) {
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+              if (k > j) A.psi[(int64_t)(k - 1) * NR + gi] = z[k];
+          }
+        }
+        const float wdt = a1[u] * A.wscale;
+        const float d1 = fmaf(A.sc, psi, fmaf(A.kc, g1, wdt));
+        const uint32_t tp = t0[u] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+        if (ok[u]) {
+          A.theta_t[gi] = tp;
+          A.y[gi] = fmaf(A.sc, psi, fmaf(A.kh, g1, wdt));
+        }
+        sincos_turns(tp, sn, cs);
+      } else {
+        float s2, c2;
+        sincos_turns(tt[u], s2, c2);
+        const float g2 = c2 * S - s2 * C;
+        const uint32_t t1 = t0[u] + (uint32_t)__float2int_rn(fmaf(A.kh, g2, a1[u]) * 4294967296.0f);
+        if (ok[u]) A.theta[gi] = t1;
+        sincos_turns(t1, sn, cs);
+      }
+      if (ok[u]) {
+        ps += sn;
+        pc += cs;
+      }
+    }
+  }
+  const float2 b = block_sum2(ps, pc, red);
+  if (threadIdx.x == 0) {
+    A.partials[(int64_t)rep * gridDim.x + blockIdx.x] = b;
+    __threadfence();
+    is_last = atomicAdd(&A.count[rep], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double s = 0.0, c = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += kMfgThreads) {
+    const float2 p = __ldcg(&A.partials[(int64_t)rep * gridDim.x + q]);
+    s += p.x;
+    c += p.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red64[warp] = make_double2(s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S64 = 0.0, C64 = 0.0;
+    for (int w = 0; w < kMfgThreads / 32; ++w) {
+      S64 += red64[w].x;
+      C64 += red64[w].y;
+    }
+    if (MODE == 0) {
+      tot[2] = S64;
+      tot[3] = C64;
+    } else {
+      tot[0] = S64;
+      tot[1] = C64;
+      if (A.sample_row >= 0 && A.r_out)
+        A.r_out[A.sample_row * A.R + rep] = sqrt(S64 * S64 + C64 * C64) / (double)N;
+    }
+    A.count[rep] = 0u;
+  }
 }
 
 // ---- pairwise form (Alg. 3) --------------------------------------------
@@ -371,7 +534,7 @@ __global__ void kur_order_kernel(const uint32_t *theta, int64_t N, int64_t R, do
   float S = 0.0f, C = 0.0f;
   for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
     float sn, cs;
-    sincospif(2.0f * ((float)(int32_t)theta[(int64_t)rep * N + i] * 2.3283064365386963e-10f), &sn, &cs);
+    sincos_turns(theta[(int64_t)rep * N + i], sn, cs);
     S += sn;
     C += cs;
   }
@@ -498,6 +661,34 @@ cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, int cs, cudaS
   return cudaGetLastError();
 }
 
+// Blocks per replica of the grid-wide mean field: enough oscillators per
+// thread to amortise the reduction, about eight blocks per SM in total.
+// One full wave of each kernel (resident blocks per SM from the occupancy
+// calculator x SMs, shared among the replicas), at most one block per
+// kMfgThreads x kMfgIlp oscillators.
+void mfg_grid_for(int64_t N, int64_t R, int sm_count, int grid[3]) {
+  const void *fn[3] = {(const void *)kur_mfg_kernel<0>, (const void *)kur_mfg_kernel<1>,
+                       (const void *)kur_mfg_kernel<2>};
+  const int64_t need = (N + kMfgThreads * kMfgIlp - 1) / (kMfgThreads * kMfgIlp);
+  for (int m = 0; m < 3; ++m) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn[m], kMfgThreads, 0) != cudaSuccess)
+      per_sm = 4;
+    const int64_t fill = std::max<int64_t>(1, ((int64_t)std::max(1, per_sm) * sm_count + R - 1) / R);
+    grid[m] = (int)std::max<int64_t>(1, std::min<int64_t>(need, fill));
+  }
+}
+
+cudaError_t launch_mfg(const MfgArgs &a, int mode, int blocks, cudaStream_t s) {
+  const dim3 grid((unsigned)blocks, (unsigned)a.R);
+  switch (mode) {
+    case 0: kur_mfg_kernel<0><<<grid, kMfgThreads, 0, s>>>(a); break;
+    case 1: kur_mfg_kernel<1><<<grid, kMfgThreads, 0, s>>>(a); break;
+    default: kur_mfg_kernel<2><<<grid, kMfgThreads, 0, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
 int pow2_at_least(int64_t x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -535,10 +726,64 @@ std::vector<MfShape> meanfield_candidates(int64_t N) {
 
 }  // namespace
 
+MfgArgs mfg_args(KuramotoCtx *k, const float *omega, double *rbuf) {
+  const double inv2pi = 0.15915494309189533577;
+  MfgArgs a{};
+  a.theta = k->theta;
+  a.theta_t = k->theta_t;
+  a.y = k->g1;
+  a.psi = k->psi4;
+  a.omega = omega;
+  a.partials = k->mfg_partials;
+  a.tot = k->mfg_tot;
+  a.count = k->mfg_count;
+  a.r_out = rbuf;
+  a.N = k->N;
+  a.R = k->R;
+  a.wscale = (float)(k->dt * inv2pi);
+  a.kc = (float)(k->K / (double)k->N * k->dt * inv2pi);
+  a.kh = (float)(0.5 * k->K / (double)k->N * k->dt * inv2pi);
+  a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
+  a.keys = philox_round_keys(k->seed);
+  return a;
+}
+
+// Steps [n_begin, n_end) of the grid-wide mean field: the sums of theta at
+// n_begin, then predictor and corrector launches per step.  r(t) rows as in
+// the single-CTA form: every M steps from n_begin, plus n_end as the last row.
+sde_status run_meanfield_grid(KuramotoCtx *k, int64_t n_begin, int64_t n_end, const float *omega,
+                              double *rbuf, int64_t n_rows, cudaStream_t s) {
+  MfgArgs a = mfg_args(k, omega, rbuf);
+  const int *grid = k->mfg_grid;
+  a.n = n_begin;
+  a.sample_row = n_rows > 0 ? 0 : -1;
+  SDE_CUDA_TRY(launch_mfg(a, 2, grid[2], s));
+  for (int64_t n = n_begin; n < n_end; ++n) {
+    a.n = n;
+    a.gen = (n == n_begin || (n & 3) == 0) ? 1 : 0;
+    a.sample_row = -1;
+    SDE_CUDA_TRY(ktime_begin(k, s));
+    SDE_CUDA_TRY(launch_mfg(a, 0, grid[0], s));
+    SDE_CUDA_TRY(ktime_end(k, s));
+    const int64_t m = n + 1;
+    if (n_rows > 0) {
+      if (m == n_end)
+        a.sample_row = n_rows - 1;
+      else if ((m - n_begin) % k->M == 0)
+        a.sample_row = (m - n_begin) / k->M;
+    }
+    SDE_CUDA_TRY(ktime_begin(k, s));
+    SDE_CUDA_TRY(launch_mfg(a, 1, grid[1], s));
+    SDE_CUDA_TRY(ktime_end(k, s));
+  }
+  return SDE_OK;
+}
+
 // Time a short run of every candidate shape on scratch phases and keep the
 // fastest.
-sde_status meanfield_autotune(KuramotoCtx *k, int only_cs) {
+sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
   auto cands = meanfield_candidates(k->N);
+  if (with_grid && only_cs == 0) cands.push_back({0, kMfgThreads, 0});
   if (only_cs > 0) {
     std::vector<MfShape> keep;
     for (const auto &c : cands)
@@ -583,7 +828,13 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs) {
       float tmin = 1e30f;
       for (int rep = 0; rep < 3 && st == SDE_OK; ++rep) {
         cudaEventRecord(e0, s);
-        if ((e = launch_meanfield(a, c.block, c.opt, c.cs, s)) != cudaSuccess) {
+        if (c.cs == 0) {
+          const uint32_t flags = k->flags;
+          k->flags &= ~SDE_FLAG_TIME_KERNELS;
+          st = run_meanfield_grid(k, a.n_begin, a.n_end, omega, nullptr, 0, s);
+          k->flags = flags;
+          if (st != SDE_OK) break;
+        } else if ((e = launch_meanfield(a, c.block, c.opt, c.cs, s)) != cudaSuccess) {
           st = cuda_fail(e, "mean-field autotune launch");
           break;
         }
@@ -621,8 +872,18 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   SDE_CHECK_ARG(cfg->dt > 0.0, "dt must be > 0");
   SDE_CHECK_ARG(cfg->sample_every >= 0, "sample_every must be >= 0");
   SDE_CHECK_ARG(cfg->n_osc < (1ll << 31), "n_osc too large");
-  if (cfg->model == SDE_KURAMOTO_MEANFIELD)
-    SDE_CHECK_ARG(cfg->n_osc <= 8192, "mean-field form holds a replica in one CTA: n_osc <= 8192");
+  const bool mf = cfg->model == SDE_KURAMOTO_MEANFIELD;
+  if (mf)
+    SDE_CHECK_ARG(cfg->schedule == SDE_SCHED_PERSISTENT || cfg->schedule == SDE_SCHED_GRID,
+                  "mean-field schedule must be SDE_SCHED_PERSISTENT (choose the form) or SDE_SCHED_GRID");
+  else
+    SDE_CHECK_ARG(cfg->schedule == SDE_SCHED_PERSISTENT, "schedule must be 0 for this Kuramoto model");
+  // Forms of the mean field: a replica per CTA or cluster (n_osc <= 8192), or
+  // spread over the whole grid (any n_osc; forced by SDE_SCHED_GRID).
+  const bool grid_forced = mf && (cfg->schedule == SDE_SCHED_GRID || cfg->n_osc > 8192);
+  if (grid_forced)
+    SDE_CHECK_ARG(cfg->cluster_ctas == 0 && cfg->block_threads == 0,
+                  "the grid-wide mean field takes cluster_ctas = 0 and block_threads = 0");
   KuramotoCtx *k = new (std::nothrow) KuramotoCtx();
   if (!k) {
     set_error("host allocation failed");
@@ -647,9 +908,22 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
     if ((e = cudaMalloc(p, bytes ? bytes : 1)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
   };
   alloc((void **)&k->theta, NR * 4);
-  if (cfg->model == SDE_KURAMOTO_PAIRWISE) {
+  // the grid-wide form is a candidate when few replicas leave SMs idle
+  const bool grid_possible =
+      mf && (grid_forced || (cfg->cluster_ctas == 0 && cfg->block_threads == 0 && cfg->n_replicas * 4 < sm_count));
+  if (cfg->model == SDE_KURAMOTO_PAIRWISE || grid_possible) {
     alloc((void **)&k->theta_t, NR * 4);
     alloc((void **)&k->g1, NR * 4);
+  }
+  if (grid_possible) {
+    mfg_grid_for(k->N, k->R, sm_count, k->mfg_grid);
+    k->mfg_blocks = std::max(k->mfg_grid[0], std::max(k->mfg_grid[1], k->mfg_grid[2]));
+    alloc((void **)&k->mfg_partials, sizeof(float2) * (size_t)k->mfg_blocks * (size_t)k->R);
+    alloc((void **)&k->mfg_tot, sizeof(double) * 4 * (size_t)k->R);
+    alloc((void **)&k->mfg_count, sizeof(uint32_t) * (size_t)k->R);
+    alloc((void **)&k->psi4, sizeof(float) * 3 * NR);
+    if (st == SDE_OK && (e = cudaMemset(k->mfg_count, 0, sizeof(uint32_t) * (size_t)k->R)) != cudaSuccess)
+      st = cuda_fail(e, "cudaMemset");
   }
   if (st == SDE_OK && (cfg->model == SDE_KURAMOTO_GENERAL || cfg->model == SDE_KURAMOTO_GENERAL_FP32))
     st = kuramoto_general_alloc(k);
@@ -661,8 +935,11 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   SDE_CHECK_ARG(cfg->cluster_ctas == 0 || cfg->cluster_ctas == 1 || cfg->cluster_ctas == 2 ||
                     cfg->cluster_ctas == 4,
                 "cluster_ctas must be 0, 1, 2 or 4");
-  if (cfg->model == SDE_KURAMOTO_MEANFIELD && cfg->block_threads == 0) {
-    st = meanfield_autotune(k, cfg->cluster_ctas);
+  if (grid_forced) {
+    k->cs = 0;
+    k->block = kMfgThreads;
+  } else if (cfg->model == SDE_KURAMOTO_MEANFIELD && cfg->block_threads == 0) {
+    st = meanfield_autotune(k, cfg->cluster_ctas, grid_possible);
     if (st != SDE_OK) {
       kuramoto_destroy(k);
       return st;
@@ -688,7 +965,11 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
 
 void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread, int32_t *cluster) {
   if (block) *block = k->block;
-  if (per_thread) *per_thread = k->opt;
+  if (per_thread)
+    *per_thread = (k->model == SDE_KURAMOTO_MEANFIELD && k->cs == 0)
+                      ? (int32_t)((k->N + (int64_t)k->mfg_grid[0] * kMfgThreads - 1) /
+                                  ((int64_t)k->mfg_grid[0] * kMfgThreads))
+                      : k->opt;
   if (cluster) *cluster = k->cs;
 }
 
@@ -733,6 +1014,9 @@ void kuramoto_destroy(KuramotoCtx *k) {
   cudaFree(k->theta_t);
   cudaFree(k->g1);
   cudaFree(k->r_scratch);
+  cudaFree(k->mfg_partials);
+  cudaFree(k->mfg_tot);
+  cudaFree(k->mfg_count);
   kuramoto_general_free(k);
   delete k;
 }
@@ -770,7 +1054,10 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
   const double inv2pi = 0.15915494309189533577;
   k->kev_used = 0;
   SDE_CUDA_TRY(cudaEventRecord(ev0, s));
-  if (k->model == SDE_KURAMOTO_MEANFIELD) {
+  if (k->model == SDE_KURAMOTO_MEANFIELD && k->cs == 0) {
+    sde_status st = run_meanfield_grid(k, r->n_begin, r->n_end, r->omega_dev, rbuf, n_rows, s);
+    if (st != SDE_OK) return st;
+  } else if (k->model == SDE_KURAMOTO_MEANFIELD) {
     KurArgs a{};
     a.theta_in = k->theta;
     a.theta_out = k->theta;

@@ -22,11 +22,18 @@ struct KuramotoCtx {
   uint32_t *err = nullptr;
   uint32_t flags = 0;
   int block = 0, opt = 0;
-  int cs = 1;  // mean field: CTAs per replica (thread-block cluster size)
+  int cs = 1;  // mean field: CTAs per replica (thread-block cluster size); 0 = grid-wide form
+  // grid-wide mean field: per-replica partial sums, totals and block counters
+  int mfg_blocks = 0;             // blocks per replica, the largest of mfg_grid
+  int mfg_grid[3] = {0, 0, 0};    // blocks per replica of the predictor, corrector, sums kernels
+  float2 *mfg_partials = nullptr; // [R][mfg_blocks]
+  double *mfg_tot = nullptr;      // [R][4]: S, C of theta_n, then S, C of theta~_n
+  uint32_t *mfg_count = nullptr;  // [R]
   // phases as fixed-point turns, [R][N]
   uint32_t *theta = nullptr;
-  uint32_t *theta_t = nullptr;  // predictor phases (pairwise, general)
-  float *g1 = nullptr;          // first-stage coupling sums (pairwise, general)
+  uint32_t *theta_t = nullptr;  // predictor phases (pairwise, general, grid-wide mean field)
+  float *g1 = nullptr;          // first-stage coupling sums (pairwise, general); grid-wide
+                                // mean field: the first-stage part of the step increment
   double *r_scratch = nullptr;  // r samples when the caller passes none
   int64_t r_scratch_rows = 0;
   // general coupling

@@ -111,6 +111,16 @@ __device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uin
   return (n & 1) ? z1 : z0;
 }
 
+// gauss1 with precomputed round keys.
+__device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uint32_t tag,
+                                        const PhiloxKeys &K) {
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 2), c1, c2, tag), K);
+  const bool hi = (n & 2) != 0;
+  float z0, z1;
+  box_muller(hi ? r.z : r.x, hi ? r.w : r.y, z0, z1);
+  return (n & 1) ? z1 : z0;
+}
+
 // Element k (0..3) of a 4-vector without dynamic register indexing.
 __device__ __forceinline__ float pick4(const float (&z)[4], int k) {
   return k == 0 ? z[0] : (k == 1 ? z[1] : (k == 2 ? z[2] : z[3]));

@@ -20,6 +20,10 @@ Workloads (sizes as used by the tests and the benchmark):
   dt 0.01, 10^4 steps, samples of r every 100 steps.
 - ``kuramoto_general``: N 8192, 256 replicas, K_ij = (K0 / N)(1 + 0.5 u_ij),
   u_ij ~ U[-1, 1], K0 3, D 0.02, dt 0.005, 5000 steps.
+- ``josephson_fig2``: the Fig. 2 ensemble, 2^19 paths at the parameters above,
+  dt = (2 pi / omega) / 100, 2 10^5 steps.
+- ``kuramoto_fig4``: the Fig. 4 ensemble, one replica of 2^24 oscillators,
+  omega_i = 0, K 4, D 1, dt 0.01, 2000 steps, samples every 100.
 """
 import math
 
@@ -41,6 +45,19 @@ def josephson_plain(paths=1024, steps=20_000, seed=0):
         x0=x0,
         v0=v0,
     )
+
+
+def josephson_fig2(paths=2 ** 19, periods=2000, steps_per_period=100, seed=0):
+    """The ensemble of the paper's Fig. 2: 524,288 paths of Eq. 1 at a = 4.2,
+    gamma = 0.9, omega = 4.9, D = 0.001, f = 0.1, dt = 0.01 (2 pi / omega),
+    t in (0, 2000 (2 pi / omega)): 2e5 steps."""
+    rng = np.random.default_rng(seed)
+    steps = periods * steps_per_period
+    return dict(points=[dict(gamma=0.9, a=4.2, omega=4.9, f=0.1, D=1e-3)],
+                paths=np.array([paths], dtype=np.int64), steps=np.array([steps], dtype=np.int64),
+                steps_per_period=steps_per_period, seed=seed,
+                x0=rng.random(paths).astype(np.float32),
+                v0=rng.uniform(-2.0, 2.0, paths).astype(np.float32))
 
 
 def sweep_grid(n_points=512, n_f=171, D_values=(1e-4, 1e-3, 1e-2)):
@@ -103,6 +120,16 @@ def kuramoto_general(n_osc=8192, replicas=256, K0=3.0, D=0.02, dt=0.005, steps=5
     Kmat *= np.float32(K0 / n_osc)
     return dict(n_osc=n_osc, replicas=replicas, K0=K0, D=D, dt=dt, steps=steps,
                 sample_every=sample_every, seed=seed, omega=omega, phi0=phi0, Kmat=Kmat)
+
+
+def kuramoto_fig4(n_osc=2 ** 24, K=4.0, D=1.0, dt=0.01, steps=2000, sample_every=100, seed=0):
+    """The ensemble of the paper's Fig. 4: one replica of 2^24 identical
+    oscillators (omega_i = 0), K = 4, T = 1, phases uniform on [0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    phi0 = rng.uniform(0.0, TWO_PI, (1, n_osc)).astype(np.float32)
+    omega = np.zeros((1, n_osc), dtype=np.float32)
+    return dict(n_osc=n_osc, replicas=1, K=K, D=D, dt=dt, steps=steps, sample_every=sample_every,
+                seed=seed, omega=omega, phi0=phi0)
 
 
 SURROGATE_BOX = dict(a=(0.0, 8.0), omega=(1.0, 10.0), f=(0.0, 1.0), gamma=(0.5, 2.0),

@@ -25,6 +25,7 @@ SDE_KURAMOTO_GENERAL_FP32 = 4
 
 SDE_SCHED_PERSISTENT = 0
 SDE_SCHED_PLAIN = 1
+SDE_SCHED_GRID = 2
 
 SDE_FLAG_NO_GRAPH = 1
 SDE_FLAG_TIME_KERNELS = 2
@@ -208,9 +209,10 @@ class Ensemble:
 
     @classmethod
     def kuramoto(cls, model, n_osc, n_replicas, K, D, dt, seed, sample_every=100, block_threads=0,
-                 flags=0, cluster_ctas=0):
+                 flags=0, cluster_ctas=0, schedule=SDE_SCHED_PERSISTENT):
         cfg = Config()
         cfg.model = model
+        cfg.schedule = schedule
         cfg.seed = seed
         cfg.n_osc = n_osc
         cfg.n_replicas = n_replicas
