@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
 // ---- mean field over the whole grid ------------------------------------
 
 constexpr int kMfgThreads = 256;
-constexpr int kMfgIlp = 2;  // oscillators per thread per iteration (loads issued together)
+constexpr int kMfgIlp = 4;  // oscillators per thread per iteration (loads issued together)
 
 struct MfgArgs {
   uint32_t *theta;    // [R][N] theta_n; the corrector overwrites it with theta_{n+1}
@@ -308,23 +308,25 @@ struct MfgArgs {
   int64_t N, R;
   int64_t n;           // step index (noise counter)
   int64_t sample_row;  // r row written from this launch's totals, -1 = none
-  int32_t gen;         // predictor: draw the Philox block of step n (first step of a block or of a run)
   float wscale, kc, kh, sc;
   PhiloxKeys keys;
 };
 
-// MODE 2: sums of (sin, cos) of theta_n.  MODE 0 (predictor): g1 from the
+// MODE 2: sums of (sin, cos) of theta_n.  MODE 0 and 3 (predictor): g1 from the
 // totals of theta_n, theta~ = theta + d1, sums over theta~.  MODE 1
 // (corrector): g2 from the totals of theta~, theta_{n+1} = theta + y + kh g2,
 // sums over theta_{n+1} (the next step's first-stage sums).  The Gaussian of
 // step n is element n mod 4 of the Philox block n / 4 of the oscillator (as
-// in the other forms): the predictor draws the block at its first step and
-// keeps the later elements in `psi` for the next three steps.  Each thread
+// in the other forms): the predictor draws the block at its first step, or
+// at the first step of a run (MODE 3), and keeps the later elements in `psi`
+// for the next three steps (MODE 0 reads them).  Each thread
 // strides over the replica; the block's FP32 sums go to `partials`, and the
 // block that finishes last adds all partials of the replica in block order
 // in FP64, so the totals do not depend on which block that is.
 template <int MODE>
-__global__ void __launch_bounds__(kMfgThreads) kur_mfg_kernel(const MfgArgs A) {
+__global__ void __launch_bounds__(kMfgThreads, MODE == 3 ? 4 : (MODE == 2 ? 8 : 5)) kur_mfg_kernel(const MfgArgs A) {
+  constexpr bool kPred = MODE == 0 || MODE == 3;
+  constexpr bool kGen = MODE == 3;
   __shared__ float2 red[32];
   __shared__ double2 red64[32];
   __shared__ bool is_last;
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(kMfgThreads) kur_mfg_kernel(const MfgArgs A) {
   const int64_t base = (int64_t)rep * N;
   double *tot = A.tot + 4 * rep;
   float S = 0.0f, C = 0.0f;
-  if (MODE == 0) {
+  if (kPred) {
     S = (float)tot[0];
     C = (float)tot[1];
   } else if (MODE == 1) {
@@ -354,9 +356,9 @@ __global__ void __launch_bounds__(kMfgThreads) kur_mfg_kernel(const MfgArgs A) {
       ok[u] = i < N;
       const int64_t gi = base + (ok[u] ? i : 0);
       t0[u] = A.theta[gi];
-      if (MODE == 0) {
+      if (kPred) {
         a1[u] = A.omega[gi];
-        a2[u] = A.gen ? 0.0f : A.psi[(int64_t)(j - 1) * NR + gi];
+        a2[u] = kGen ? 0.0f : A.psi[(int64_t)(j - 1) * NR + gi];
       } else if (MODE == 1) {
         tt[u] = A.theta_t[gi];
         a1[u] = A.y[gi];
@@ -369,12 +371,12 @@ __global__ void __launch_bounds__(kMfgThreads) kur_mfg_kernel(const MfgArgs A) {
       float sn, cs;
       if (MODE == 2) {
         sincos_turns(t0[u], sn, cs);
-      } else if (MODE == 0) {
+      } else if (kPred) {
         float s0, c0;
         sincos_turns(t0[u], s0, c0);
         const float g1 = c0 * S - s0 * C;
         float psi = a2[u];
-        if (A.gen) {
+        if (kGen) {
           float z[4];
           gauss4((uint32_t)(A.n >> 2), (uint32_t)i, (uint32_t)rep, kTagKuramoto, A.keys, z);
           psi = pick4(z, j);
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kMfgThreads) kur_mfg_kernel(const MfgArgs A) {
       S64 += red64[w].x;
       C64 += red64[w].y;
     }
-    if (MODE == 0) {
+    if (kPred) {
       tot[2] = S64;
       tot[3] = C64;
     } else {
@@ -666,11 +668,11 @@ cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, int cs, cudaS
 // One full wave of each kernel (resident blocks per SM from the occupancy
 // calculator x SMs, shared among the replicas), at most one block per
 // kMfgThreads x kMfgIlp oscillators.
-void mfg_grid_for(int64_t N, int64_t R, int sm_count, int grid[3]) {
-  const void *fn[3] = {(const void *)kur_mfg_kernel<0>, (const void *)kur_mfg_kernel<1>,
-                       (const void *)kur_mfg_kernel<2>};
+void mfg_grid_for(int64_t N, int64_t R, int sm_count, int grid[4]) {
+  const void *fn[4] = {(const void *)kur_mfg_kernel<0>, (const void *)kur_mfg_kernel<1>,
+                       (const void *)kur_mfg_kernel<2>, (const void *)kur_mfg_kernel<3>};
   const int64_t need = (N + kMfgThreads * kMfgIlp - 1) / (kMfgThreads * kMfgIlp);
-  for (int m = 0; m < 3; ++m) {
+  for (int m = 0; m < 4; ++m) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn[m], kMfgThreads, 0) != cudaSuccess)
       per_sm = 4;
@@ -684,6 +686,7 @@ cudaError_t launch_mfg(const MfgArgs &a, int mode, int blocks, cudaStream_t s) {
   switch (mode) {
     case 0: kur_mfg_kernel<0><<<grid, kMfgThreads, 0, s>>>(a); break;
     case 1: kur_mfg_kernel<1><<<grid, kMfgThreads, 0, s>>>(a); break;
+    case 3: kur_mfg_kernel<3><<<grid, kMfgThreads, 0, s>>>(a); break;
     default: kur_mfg_kernel<2><<<grid, kMfgThreads, 0, s>>>(a); break;
   }
   return cudaGetLastError();
@@ -760,10 +763,10 @@ sde_status run_meanfield_grid(KuramotoCtx *k, int64_t n_begin, int64_t n_end, co
   SDE_CUDA_TRY(launch_mfg(a, 2, grid[2], s));
   for (int64_t n = n_begin; n < n_end; ++n) {
     a.n = n;
-    a.gen = (n == n_begin || (n & 3) == 0) ? 1 : 0;
+    const int pred = (n == n_begin || (n & 3) == 0) ? 3 : 0;
     a.sample_row = -1;
     SDE_CUDA_TRY(ktime_begin(k, s));
-    SDE_CUDA_TRY(launch_mfg(a, 0, grid[0], s));
+    SDE_CUDA_TRY(launch_mfg(a, pred, grid[pred], s));
     SDE_CUDA_TRY(ktime_end(k, s));
     const int64_t m = n + 1;
     if (n_rows > 0) {
@@ -917,7 +920,7 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   }
   if (grid_possible) {
     mfg_grid_for(k->N, k->R, sm_count, k->mfg_grid);
-    k->mfg_blocks = std::max(k->mfg_grid[0], std::max(k->mfg_grid[1], k->mfg_grid[2]));
+    k->mfg_blocks = *std::max_element(k->mfg_grid, k->mfg_grid + 4);
     alloc((void **)&k->mfg_partials, sizeof(float2) * (size_t)k->mfg_blocks * (size_t)k->R);
     alloc((void **)&k->mfg_tot, sizeof(double) * 4 * (size_t)k->R);
     alloc((void **)&k->mfg_count, sizeof(uint32_t) * (size_t)k->R);

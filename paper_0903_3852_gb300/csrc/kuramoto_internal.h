@@ -25,7 +25,7 @@ struct KuramotoCtx {
   int cs = 1;  // mean field: CTAs per replica (thread-block cluster size); 0 = grid-wide form
   // grid-wide mean field: per-replica partial sums, totals and block counters
   int mfg_blocks = 0;             // blocks per replica, the largest of mfg_grid
-  int mfg_grid[3] = {0, 0, 0};    // blocks per replica of the predictor, corrector, sums kernels
+  int mfg_grid[4] = {0, 0, 0, 0}; // blocks per replica: predictor, corrector, sums, predictor drawing noise
   float2 *mfg_partials = nullptr; // [R][mfg_blocks]
   double *mfg_tot = nullptr;      // [R][4]: S, C of theta_n, then S, C of theta~_n
   uint32_t *mfg_count = nullptr;  // [R]

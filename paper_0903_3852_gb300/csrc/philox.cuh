@@ -12,9 +12,13 @@
 // Uniforms take the top 24 bits of a word: u = ((w >> 8) + 1) * 2^-24, in
 // (0, 1] and exact in FP32.  Box-Muller (Sec. 4.1, two uniforms -> two
 // Gaussians): z0 = sqrt(-2 ln u0) cos(2 pi u1), z1 = sqrt(-2 ln u0) sin(2 pi u1).
+// The angle u1 is a 24-bit fraction of a turn, so its sine and cosine are
+// taken from the fixed-point value ((w1 >> 8) + 1) * 2^8 directly.
 #pragma once
 
 #include <stdint.h>
+
+#include "turns.cuh"
 
 namespace sde {
 
@@ -73,13 +77,12 @@ __device__ __forceinline__ float uniform24(uint32_t w) {
 
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1) {
   const float u0 = uniform24(w0);
-  const float u1 = uniform24(w1);
   // sqrt(L) as L rsqrt(L) (two instructions, within 2 ulp); L = 0 exactly
   // when u0 = 1, which 1 in 2^24 draws hit
   const float L = -2.0f * logf(u0);
   const float rho = L > 0.0f ? L * rsqrtf(L) : 0.0f;
   float s, c;
-  sincospif(2.0f * u1, &s, &c);
+  sincos_turns(((w1 >> 8) + 1u) << 8, s, c);
   z0 = rho * c;
   z1 = rho * s;
 }

@@ -67,7 +67,7 @@ def test_box_muller_matches_oracle():
         ref[i, 0:2] = oracle.box_muller(w[i, 0], w[i, 1])
         ref[i, 2:4] = oracle.box_muller(w[i, 2], w[i, 3])
     err = np.abs(z - ref)
-    # identical uniforms; FP32 log, sqrt and sincospi each within a few ulp
+    # identical uniforms; FP32 log, sqrt and the fixed-point sin/cos each within a few ulp
     assert np.all(err <= 6e-7 * np.abs(ref) + 2e-7), err.max()
     # the stream layout the integrators use: Gaussian of step n from block n/4
     g = [oracle.gaussian(seed, int(c[1, 3]), int(c[1, 1]), int(c[1, 2]), 4 * int(c[1, 0]) + k)
