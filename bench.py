@@ -45,12 +45,14 @@ def parse():
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise",
                              "kuramoto-general", "kuramoto-general-fp32", "surrogate", "fig2",
-                             "kuramoto-fig4"])
+                             "kuramoto-fig4", "fig2-fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairwise-steps", type=int, default=200,
                     help="steps per bench step of the pairwise Kuramoto workload")
     ap.add_argument("--fig4-steps", type=int, default=None,
                     help="kuramoto-fig4: steps per bench step (default: the workload's 2000)")
+    ap.add_argument("--fp64-steps", type=int, default=20_000,
+                    help="fig2-fp64: steps of the FP64 run per bench step (the Fig. 2 run has 2e5)")
     ap.add_argument("--general-steps", type=int, default=0,
                     help="steps per bench step of the general-coupling workloads "
                          "(default: all 5000 for BF16, 100 for the FP32 baseline)")
@@ -154,6 +156,9 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
+
+
 def fp32_peak_tflops(props):
     # 128 FP32 lanes per SM on Blackwell, one FMA (2 FLOP) per lane per clock,
     # at the maximum SM clock of 2070 MHz.
@@ -213,6 +218,59 @@ def run_ours(args, rank, world, device):
                "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
                "tuning": dict(zip(("block_threads", "paths_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write); state 9 MB, compute-bound"}
+    elif args.workload == "fig2-fp64":
+        # the Fig. 2 ensemble in double precision on the GPU (Sec. 5's DP run),
+        # shortened to --fp64-steps steps
+        w = fig2_workload(rank)
+        S = args.fp64_steps
+        n = int(w["paths"][0])
+        pt = w["points"][0]
+        P = w["steps_per_period"]
+        x_h = torch.from_numpy(w["x0"].astype(np.float64)).pin_memory()
+        v_h = torch.from_numpy(w["v0"].astype(np.float64)).pin_memory()
+        x_in, v_in = x_h.to(device), v_h.to(device)
+        x_out, v_out = torch.empty_like(x_in), torch.empty_like(v_in)
+        vs_out = torch.empty_like(x_in)
+        v_back = torch.empty(n, dtype=torch.float64).pin_memory()
+
+        class _Timed:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+
+            def close(self):
+                pass
+
+            def last_kernel_stats(self):
+                self.e1.synchronize()
+                t = self.e0.elapsed_time(self.e1)
+                return t, t, 1
+
+        ens = _Timed()
+
+        def step():
+            ens.e0.record(stream)
+            sde.josephson_run_fp64(pt, P, S, w["seed"], 0, S, x_in, v_in, x_out, v_out, vsum_out=vs_out,
+                                   stream=stream)
+            ens.e1.record(stream)
+
+        def step_e2e():
+            x_in.copy_(x_h, non_blocking=True)
+            v_in.copy_(v_h, non_blocking=True)
+            step()
+            v_back.copy_(v_out, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return v_back
+
+        h2d = 16 * n
+        d2h = 8 * n
+        units = float(n * S)
+        metric = "path-steps/sec"
+        launches_per_step = 1
+        flop_per_unit = PAPER_FLOP_PER_STEP
+        flop_per_launch = flop_per_unit * units
+        cfg = {"workload": "josephson_fig2_fp64_%dpaths_%dsteps" % (n, S), "precision": "fp64 throughout",
+               "steps_per_period": P, "full_run_steps": int(w["steps"][0]),
+               "l2": "flushed between steps (256 MiB write); state 8 MB, compute-bound"}
     elif args.workload in ("kuramoto-meanfield", "kuramoto-pairwise", "kuramoto-fig4"):
         fig4 = args.workload == "kuramoto-fig4"
         w = inputs.kuramoto_fig4(seed=rank) if fig4 else inputs.kuramoto_uniform(seed=rank)
@@ -361,6 +419,10 @@ def run_ours(args, rank, world, device):
         bound, peak = "hbm", peaks["hbm_gbs"]
         peak_note = "HBM copy bandwidth, %s" % peak_src
         flop_note = "16 B per oscillator per stage launch (theta, omega or theta~, y read; theta~, y or theta written)"
+    elif args.workload == "fig2-fp64":
+        bound, peak = "alu", FP64_PEAK_TFLOPS
+        peak_note = "FP64 1.25 TFLOP/s nominal (no measured FP64 peak)"
+        flop_note = "%d FLOP per path-step (paper Table 1 weighting), in FP64" % flop_per_unit
     elif args.workload == "kuramoto-general":
         bound, peak = "tensor", peaks["bf16_tflops_sustained"]
         peak_note = "bf16 dense, sustained, %s" % peak_src
@@ -393,7 +455,7 @@ def run_ours(args, rank, world, device):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (FP64 reductions)",
+        "dtype": "f64" if args.workload == "fig2-fp64" else "f32 (FP64 reductions)",
         "data": "synthetic (seeded; inputs.py)",
         "config": cfg,
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak,
@@ -414,10 +476,13 @@ def run_ours(args, rank, world, device):
 def cpu_baseline(args, budget_s=20.0):
     """The FP64 oracle as it stands, on a bounded sample of the workload."""
     import oracle
-    if args.workload in ("sweep", "plain", "fig2"):
-        w = {"sweep": sweep_workload, "plain": plain_workload, "fig2": fig2_workload}[args.workload](0)
+    if args.workload in ("sweep", "plain", "fig2", "fig2-fp64"):
+        w = {"sweep": sweep_workload, "plain": plain_workload, "fig2": fig2_workload,
+             "fig2-fp64": fig2_workload}[args.workload](0)
+        if args.workload == "fig2-fp64":
+            w["steps"] = np.array([args.fp64_steps], dtype=np.int64)
         offs = np.concatenate([[0], np.cumsum(w["paths"])])
-        per_point = {"sweep": 2, "plain": 64, "fig2": 256}[args.workload]
+        per_point = {"sweep": 2, "plain": 64, "fig2": 256, "fig2-fp64": 1024}[args.workload]
         t0 = time.perf_counter()
         done = 0.0
         npts = 0
@@ -486,6 +551,7 @@ def run_reference(args):
         vals.append(last["value"])
     v = statistics.mean(vals)
     metric = {"sweep": "path-steps/sec", "plain": "path-steps/sec", "fig2": "path-steps/sec",
+              "fig2-fp64": "path-steps/sec",
               "kuramoto-meanfield": "oscillator-steps/sec", "kuramoto-pairwise": "pair-terms/sec",
               "kuramoto-fig4": "oscillator-steps/sec",
               "kuramoto-general": "oscillator-steps/sec",

@@ -317,6 +317,34 @@ sde_status sde_josephson_run_noalloc(const sde_jj_point *point_host, int32_t ste
                                      int32_t *w_out_dev, double *vsum_out_dev, sde_obs_row *obs_dev,
                                      void *stream);
 
+/*
+ * Double-precision run of one Eq. 1 parameter point: Alg. 2 with every
+ * operation in FP64, the counterpart of the paper's double-precision GPU
+ * run of Fig. 2 (Sec. 5 compares its histograms with the FP32 run's).  The
+ * noise is the FP32 path's stream -- Philox4x32-10 block n / 4 of counter
+ * (path, point_index, tag 1), the same 24-bit uniforms -- with Box-Muller in
+ * FP64, so an FP32 and an FP64 run of the same point draw the same
+ * Gaussians up to FP32 rounding.
+ *
+ *  - x is the absolute position in units of the potential period (no
+ *    winding split), v the velocity; [n_paths] FP64 device arrays, caller-
+ *    owned; *_in and *_out may alias.  vsum_in / vsum_out (nullable) carry
+ *    the running sum of v over the window (S - floor(S/2), S] of state
+ *    indices, S = total_steps; the run stops at S.
+ *  - Steps [n_begin, n_end) are taken; splitting a run at any step gives
+ *    the same result bit for bit.
+ *  - err_dev (nullable, device) gets bit 1 ORed in when a path ends
+ *    non-finite.  Asynchronous on `stream`; no allocation.
+ *  - Invalid sizes or parameters return SDE_ERR_INVALID_ARG before any
+ *    CUDA call.
+ */
+sde_status sde_josephson_run_fp64(const sde_jj_point *point_host, int32_t steps_per_period,
+                                  int64_t n_paths, int64_t total_steps, uint64_t seed,
+                                  uint32_t point_index, int64_t n_begin, int64_t n_end,
+                                  const double *x_in_dev, const double *v_in_dev,
+                                  const double *vsum_in_dev, double *x_out_dev, double *v_out_dev,
+                                  double *vsum_out_dev, uint32_t *err_dev, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Learned surrogate of <<v>> (not in the paper).                          */
 /*                                                                         */

@@ -113,6 +113,9 @@ SIGNATURES = [
     ("sde_josephson_run_noalloc", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_int64, ctypes.c_int64] + [_VP] * 9 + [_VP]),
+    ("sde_josephson_run_fp64", ctypes.c_int,
+     [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+      ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64] + [_VP] * 7 + [_VP]),
 ]
 
 NOALLOC_MAX_PATHS = 1 << 20
@@ -322,6 +325,19 @@ def josephson_run_noalloc(point, steps_per_period, n_paths, total_steps, seed, n
         ctypes.byref(p), steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
         _ptr(x_in), _ptr(v_in), _ptr(w_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(w_out),
         _ptr(vsum_out), _ptr(obs_out), _stream(stream)))
+
+
+def josephson_run_fp64(point, steps_per_period, total_steps, seed, n_begin, n_end, x_in, v_in, x_out, v_out,
+                       vsum_in=None, vsum_out=None, point_index=0, err=None, stream=None):
+    """sde_josephson_run_fp64: one parameter point of Eq. 1 in FP64 on the GPU.
+    x (absolute position in potential periods) and v are float64 CUDA tensors
+    of one element per path; err: optional int32/uint32 CUDA tensor of one
+    word, bit 1 set on a non-finite state."""
+    p = JJPoint(point["gamma"], point["a"], point["omega"], point["f"], point["D"])
+    _check(lib().sde_josephson_run_fp64(
+        ctypes.byref(p), steps_per_period, x_in.numel(), total_steps, seed, point_index, n_begin, n_end,
+        _ptr(x_in), _ptr(v_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(vsum_out), _ptr(err),
+        _stream(stream)))
 
 
 SURROGATE_BOX = ((0.0, 8.0), (1.0, 10.0), (0.0, 1.0), (0.5, 2.0), (-4.0, -1.0))  # a, omega, f, gamma, log10 D

@@ -84,4 +84,12 @@ def test_validation_before_any_cuda_call(L):
     assert L.sde_box_muller(None, 0, None, 5, None) == 1
     assert L.sde_run_ensemble(None, None, None) == 1
     assert L.sde_observables(None, None, 0, None) == 1
+    assert L.sde_josephson_run_fp64(None, 100, 8, 10, 1, 0, 0, 10, None, None, None, None, None, None, None,
+                                    None) == 1
+    pt = sde.JJPoint(0.9, 4.2, 4.9, 0.1, 1e-3)
+    assert L.sde_josephson_run_fp64(ctypes.byref(pt), 0, 8, 10, 1, 0, 0, 10, None, None, None, None, None, None,
+                                    None, None) == 1
+    assert b"steps_per_period" in L.sde_last_error()
+    assert L.sde_josephson_run_fp64(ctypes.byref(pt), 100, 0, 10, 1, 0, 0, 10, None, None, None, None, None,
+                                    None, None, None) == 0  # no paths: nothing to do
     L.sde_destroy(None)  # NULL-safe
