@@ -156,7 +156,10 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
 
 
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64
+def fp64_peak_tflops(props):
+    # 2 DFMA per SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+    # peak_sustained), 2 FLOP each, at 2070 MHz
+    return props.multi_processor_count * 2 * 2 * 2.070e9 / 1e12
 
 
 def fp32_peak_tflops(props):
@@ -420,8 +423,8 @@ def run_ours(args, rank, world, device):
         peak_note = "HBM copy bandwidth, %s" % peak_src
         flop_note = "16 B per oscillator per stage launch (theta, omega or theta~, y read; theta~, y or theta written)"
     elif args.workload == "fig2-fp64":
-        bound, peak = "alu", FP64_PEAK_TFLOPS
-        peak_note = "FP64 1.25 TFLOP/s nominal (no measured FP64 peak)"
+        bound, peak = "alu", fp64_peak_tflops(props)
+        peak_note = "%d SM x 2 DFMA x 2 FLOP x 2070 MHz (derived)" % props.multi_processor_count
         flop_note = "%d FLOP per path-step (paper Table 1 weighting), in FP64" % flop_per_unit
     elif args.workload == "kuramoto-general":
         bound, peak = "tensor", peaks["bf16_tflops_sustained"]

@@ -45,7 +45,11 @@ def lib():
                                     ctypes.POINTER(JJParams), ctypes.c_int32,
                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+        L.oracle_jj_euler_step.argtypes = [_f64p, _f64p, ctypes.c_uint64, ctypes.c_double,
+                                           ctypes.POINTER(JJParams), ctypes.c_double]
+        L.oracle_jj_run_scheme.argtypes = L.oracle_jj_run.argtypes + [ctypes.c_int]
         L.oracle_linear_step.argtypes = [_f64p, _f64p] + [ctypes.c_double] * 6
+        L.oracle_linear_euler_step.argtypes = [_f64p, _f64p] + [ctypes.c_double] * 6
         L.oracle_kuramoto_coupling_direct.argtypes = [ctypes.c_int64, _f64p, _f64p,
                                                       ctypes.c_double, _f64p]
         L.oracle_kuramoto_coupling_meanfield.argtypes = [ctypes.c_int64, _f64p,
@@ -57,6 +61,7 @@ def lib():
                                           ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_uint64, ctypes.c_uint32, _f64p,
                                           ctypes.c_int64]
+        L.oracle_kuramoto_run_scheme.argtypes = L.oracle_kuramoto_run.argtypes + [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -113,6 +118,13 @@ def jj_step(x, v, n, dt, p, psi):
     return xc.value, vc.value
 
 
+def jj_euler_step(x, v, n, dt, p, psi):
+    """One Euler-Maruyama step of Eq. 1 (the first-order scheme of PROG2) -> (x, v)."""
+    xc, vc = ctypes.c_double(x), ctypes.c_double(v)
+    lib().oracle_jj_euler_step(ctypes.byref(xc), ctypes.byref(vc), n, dt, ctypes.byref(p), psi)
+    return xc.value, vc.value
+
+
 def jj_rhs(t, y, p):
     y, yp = _f64(y)
     dy = np.empty(2)
@@ -120,21 +132,31 @@ def jj_rhs(t, y, p):
     return dy
 
 
+SCHEME_SRK2, SCHEME_EULER = 0, 1
+
+
 def jj_run(x, v, p, steps_per_period, n_begin, n_end, total_steps, seed, point=0,
-           path0=0, vsum=None):
-    """Advance a batch of Eq. 1 paths (Alg. 1 with Alg. 2); returns (x, v, vsum)."""
+           path0=0, vsum=None, scheme=SCHEME_SRK2):
+    """Advance a batch of Eq. 1 paths (Alg. 1 with Alg. 2, or Euler-Maruyama
+    for scheme=SCHEME_EULER); returns (x, v, vsum)."""
     x, xp = _f64(np.array(x, dtype=np.float64, copy=True))
     v, vp = _f64(np.array(v, dtype=np.float64, copy=True))
     vs = np.zeros_like(x) if vsum is None else np.array(vsum, dtype=np.float64, copy=True)
     vs, vsp = _f64(vs)
-    lib().oracle_jj_run(x.size, xp, vp, vsp, ctypes.byref(p), steps_per_period,
-                        n_begin, n_end, total_steps, seed, point, path0)
+    lib().oracle_jj_run_scheme(x.size, xp, vp, vsp, ctypes.byref(p), steps_per_period,
+                               n_begin, n_end, total_steps, seed, point, path0, scheme)
     return x, v, vs
 
 
 def linear_step(x, v, dt, gamma, kappa, f, D, psi):
     xc, vc = ctypes.c_double(x), ctypes.c_double(v)
     lib().oracle_linear_step(ctypes.byref(xc), ctypes.byref(vc), dt, gamma, kappa, f, D, psi)
+    return xc.value, vc.value
+
+
+def linear_euler_step(x, v, dt, gamma, kappa, f, D, psi):
+    xc, vc = ctypes.c_double(x), ctypes.c_double(v)
+    lib().oracle_linear_euler_step(ctypes.byref(xc), ctypes.byref(vc), dt, gamma, kappa, f, D, psi)
     return xc.value, vc.value
 
 
@@ -163,8 +185,9 @@ def order_parameter(phi):
 
 
 def kuramoto_run(phi, omega, D, dt, n_begin, n_end, seed, replica, Kmat=None, Kconst=0.0,
-                 meanfield=False, sample_every=0):
-    """Advance one replica of Eq. 2 by SRK2; returns (phi, r samples or None)."""
+                 meanfield=False, sample_every=0, scheme=SCHEME_SRK2):
+    """Advance one replica of Eq. 2 by SRK2 (or Euler-Maruyama for
+    scheme=SCHEME_EULER); returns (phi, r samples or None)."""
     phi, pp = _f64(np.array(phi, dtype=np.float64, copy=True))
     om, op = _f64(omega)
     kp = None
@@ -176,6 +199,6 @@ def kuramoto_run(phi, omega, D, dt, n_begin, n_end, seed, replica, Kmat=None, Kc
         ns = -(-(n_end - n_begin) // sample_every)
         r = np.zeros(ns + 1)
         rp = r.ctypes.data_as(_f64p)
-    lib().oracle_kuramoto_run(phi.size, pp, op, kp, Kconst, 1 if meanfield else 0, D, dt,
-                              n_begin, n_end, seed, replica, rp, sample_every)
+    lib().oracle_kuramoto_run_scheme(phi.size, pp, op, kp, Kconst, 1 if meanfield else 0, D, dt,
+                                     n_begin, n_end, seed, replica, rp, sample_every, scheme)
     return phi, r

@@ -18,6 +18,9 @@
  *          stages):  F1 = f(x0); F2 = f(x0 + dt F1 + sqrt(2 D dt) psi);
  *          x(dt) = x0 + dt/2 (F1 + F2) + sqrt(2 D dt) psi
  *   Eq. 3  (Sec. 4.2) mean-field form of the uniform coupling sum.
+ *   Sec. 4.2          PROG2 advances with a first-order Euler scheme;
+ *          with noise this is Euler-Maruyama: x(dt) = x0 + dt f(x0) +
+ *          sqrt(2 D dt) psi (the *_euler_* functions, scheme 1).
  *   Sec. 4.1          two uniforms -> Box-Muller -> Gaussians; one RNG
  *                     stream per path.  The paper's xorshift is replaced by
  *                     Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11,
@@ -142,10 +145,24 @@ void oracle_jj_rhs(double t, const double y[2], const oracle_jj_params *p,
  * (omega * steps_per_period).  vsum accumulates v after every step whose
  * new state index n + 1 lies in the averaging window (S - W, S] with
  * W = floor(S / 2) and S = total_steps. */
-void oracle_jj_run(int64_t npaths, double *x, double *v, double *vsum,
-                   const oracle_jj_params *p, int32_t steps_per_period,
-                   uint64_t n_begin, uint64_t n_end, uint64_t total_steps,
-                   uint64_t seed, uint32_t point, uint32_t path0) {
+/* One Euler-Maruyama step of Eq. 1: the first-order scheme that the
+ * paper's PROG2 uses in its AdvanceSystem kernel (Sec. 4.2), here on
+ * (x, v): y_{n+1} = y_n + dt F(y_n, t_n) + (0, sqrt(2 gamma D dt) psi). */
+void oracle_jj_euler_step(double *x, double *v, uint64_t n, double dt,
+                          const oracle_jj_params *p, double psi) {
+  double t0 = (double)n * dt;
+  double noise = sqrt(2.0 * p->gamma * p->D * dt) * psi;
+  double Fx = *v;
+  double Fv = jj_force(*x, *v, t0, p);
+  *x = *x + dt * Fx;
+  *v = *v + dt * Fv + noise;
+}
+
+/* oracle_jj_run with the scheme chosen: 0 = SRK2 (Alg. 2), 1 = Euler-Maruyama. */
+void oracle_jj_run_scheme(int64_t npaths, double *x, double *v, double *vsum,
+                          const oracle_jj_params *p, int32_t steps_per_period,
+                          uint64_t n_begin, uint64_t n_end, uint64_t total_steps,
+                          uint64_t seed, uint32_t point, uint32_t path0, int scheme) {
   double dt = 2.0 * OR_PI / (p->omega * (double)steps_per_period);
   uint64_t wstart = total_steps - total_steps / 2; /* first index NOT in window is <= wstart */
   for (int64_t j = 0; j < npaths; ++j) {
@@ -153,13 +170,24 @@ void oracle_jj_run(int64_t npaths, double *x, double *v, double *vsum,
     for (uint64_t n = n_begin; n < n_end; ++n) {
       double psi = oracle_gaussian(seed, TAG_JOSEPHSON, path0 + (uint32_t)j,
                                    point, n);
-      oracle_jj_step(&xj, &vj, n, dt, p, psi);
+      if (scheme == 1)
+        oracle_jj_euler_step(&xj, &vj, n, dt, p, psi);
+      else
+        oracle_jj_step(&xj, &vj, n, dt, p, psi);
       if (n + 1 > wstart) sj += vj;
     }
     x[j] = xj;
     v[j] = vj;
     if (vsum) vsum[j] = sj;
   }
+}
+
+void oracle_jj_run(int64_t npaths, double *x, double *v, double *vsum,
+                   const oracle_jj_params *p, int32_t steps_per_period,
+                   uint64_t n_begin, uint64_t n_end, uint64_t total_steps,
+                   uint64_t seed, uint32_t point, uint32_t path0) {
+  oracle_jj_run_scheme(npaths, x, v, vsum, p, steps_per_period, n_begin, n_end,
+                       total_steps, seed, point, path0, 0);
 }
 
 /* Linear test drift for the weak-order check: x' = v,
@@ -173,6 +201,15 @@ void oracle_linear_step(double *x, double *v, double dt, double gamma,
   double F2x = vt, F2v = -gamma * vt - kappa * xt + f;
   *x = *x + 0.5 * dt * (F1x + F2x);
   *v = *v + 0.5 * dt * (F1v + F2v) + noise;
+}
+
+/* Euler-Maruyama step with the same linear force. */
+void oracle_linear_euler_step(double *x, double *v, double dt, double gamma,
+                              double kappa, double f, double D, double psi) {
+  double noise = sqrt(2.0 * gamma * D * dt) * psi;
+  double Fx = *v, Fv = -gamma * *v - kappa * *x + f;
+  *x = *x + dt * Fx;
+  *v = *v + dt * Fv + noise;
 }
 
 /* ------------------------------------------------------------------ */
@@ -227,11 +264,11 @@ double oracle_order_parameter(int64_t N, const double *phi) {
  * is not NULL, r(t_n) is written to r_out[(n - n_begin) / sample_every]
  * for every n in [n_begin, n_end) with (n - n_begin) % sample_every == 0,
  * and r at n_end to the slot after the last sample. */
-void oracle_kuramoto_run(int64_t N, double *phi, const double *omega,
-                         const double *Kmat, double Kconst, int use_meanfield,
-                         double D, double dt, uint64_t n_begin, uint64_t n_end,
-                         uint64_t seed, uint32_t replica, double *r_out,
-                         int64_t sample_every) {
+void oracle_kuramoto_run_scheme(int64_t N, double *phi, const double *omega,
+                                const double *Kmat, double Kconst, int use_meanfield,
+                                double D, double dt, uint64_t n_begin, uint64_t n_end,
+                                uint64_t seed, uint32_t replica, double *r_out,
+                                int64_t sample_every, int scheme) {
   double *F1 = (double *)malloc(sizeof(double) * N);
   double *F2 = (double *)malloc(sizeof(double) * N);
   double *pt = (double *)malloc(sizeof(double) * N);
@@ -244,6 +281,14 @@ void oracle_kuramoto_run(int64_t N, double *phi, const double *omega,
       oracle_kuramoto_coupling_direct(N, phi, Kmat, Kconst, F1);
     else
       oracle_kuramoto_coupling_meanfield(N, phi, Kconst, F1);
+    if (scheme == 1) {
+      /* Euler-Maruyama (PROG2's AdvanceSystem): phi += dt F(phi) + noise */
+      for (int64_t i = 0; i < N; ++i) {
+        double z = oracle_gaussian(seed, TAG_KURAMOTO, (uint32_t)i, replica, n);
+        phi[i] = phi[i] + dt * (F1[i] + omega[i]) + amp * z;
+      }
+      continue;
+    }
     for (int64_t i = 0; i < N; ++i) {
       F1[i] += omega[i];
       psi[i] = oracle_gaussian(seed, TAG_KURAMOTO, (uint32_t)i, replica, n);
@@ -266,4 +311,13 @@ void oracle_kuramoto_run(int64_t N, double *phi, const double *omega,
   free(F2);
   free(pt);
   free(psi);
+}
+
+void oracle_kuramoto_run(int64_t N, double *phi, const double *omega,
+                         const double *Kmat, double Kconst, int use_meanfield,
+                         double D, double dt, uint64_t n_begin, uint64_t n_end,
+                         uint64_t seed, uint32_t replica, double *r_out,
+                         int64_t sample_every) {
+  oracle_kuramoto_run_scheme(N, phi, omega, Kmat, Kconst, use_meanfield, D, dt,
+                             n_begin, n_end, seed, replica, r_out, sample_every, 0);
 }
