@@ -51,6 +51,8 @@ def parse():
                     help="steps per bench step of the pairwise Kuramoto workload")
     ap.add_argument("--fig4-steps", type=int, default=None,
                     help="kuramoto-fig4: steps per bench step (default: the workload's 2000)")
+    ap.add_argument("--euler", action="store_true",
+                    help="Euler-Maruyama (PROG2's scheme) instead of SRK2: Josephson workloads and kuramoto-pairwise")
     ap.add_argument("--fp64-steps", type=int, default=20_000,
                     help="fig2-fp64: steps of the FP64 run per bench step (the Fig. 2 run has 2e5)")
     ap.add_argument("--general-steps", type=int, default=0,
@@ -184,7 +186,8 @@ def run_ours(args, rank, world, device):
         sched = sde.SDE_SCHED_PLAIN if args.workload == "plain" else sde.SDE_SCHED_PERSISTENT
         ens = sde.Ensemble.josephson(w["points"], w["paths"], w["steps"], w["seed"],
                                      steps_per_period=w["steps_per_period"], schedule=sched,
-                                     block_threads=args.block, paths_per_thread=args.ilp)
+                                     block_threads=args.block, paths_per_thread=args.ilp,
+                                     flags=sde.SDE_FLAG_EULER if args.euler else 0)
         n = int(w["paths"].sum())
         units = float((w["paths"] * w["steps"]).sum())
         n_end = int(w["steps"].max())
@@ -215,6 +218,8 @@ def run_ours(args, rank, world, device):
                 "fig2": "josephson_fig2_524288paths_2e5steps"}[args.workload]
         if args.steps_cap:
             name += "_cap%d" % args.steps_cap
+        if args.euler:
+            name += "_euler"
         cfg = {"workload": name,
                "points": len(w["points"]), "total_paths": n, "path_steps": units,
                "steps_per_period": w["steps_per_period"],
@@ -281,8 +286,10 @@ def run_ours(args, rank, world, device):
         S = w["steps"] if model == sde.SDE_KURAMOTO_MEANFIELD else args.pairwise_steps
         if fig4 and args.fig4_steps:
             S = args.fig4_steps
+        euler = args.euler and model == sde.SDE_KURAMOTO_PAIRWISE
         ens = sde.Ensemble.kuramoto(model, w["n_osc"], w["replicas"], w["K"], w["D"], w["dt"], w["seed"],
-                                    sample_every=w["sample_every"], flags=sde.SDE_FLAG_TIME_KERNELS)
+                                    sample_every=w["sample_every"],
+                                    flags=sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_EULER if euler else 0))
         phi_h = torch.from_numpy(w["phi0"]).pin_memory()
         phi_in = phi_h.to(device)
         om = torch.from_numpy(w["omega"]).to(device)
@@ -315,8 +322,8 @@ def run_ours(args, rank, world, device):
             flop_per_unit = 6  # Appendix: 44 + 6N FLOP per oscillator-step, 6 per pair term
             launches_per_step = 2 * S + S // w["sample_every"] + 4
             flop_per_launch = flop_per_unit * w["n_osc"] ** 2 * w["replicas"]  # one stage launch
-        cfg = {"workload": "kuramoto_%s_N%d_R%d" % ("fig4_meanfield_grid" if fig4 else args.workload.split("-")[1],
-                                                    w["n_osc"], w["replicas"]),
+        cfg = {"workload": "kuramoto_%s_N%d_R%d%s" % ("fig4_meanfield_grid" if fig4 else args.workload.split("-")[1],
+                                                      w["n_osc"], w["replicas"], "_euler_prog2" if euler else ""),
                "steps_per_bench_step": S, "K": w["K"], "D": w["D"], "dt": w["dt"],
                "tuning": dict(zip(("block_threads", "oscillators_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write)"}

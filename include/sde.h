@@ -76,6 +76,14 @@ typedef enum sde_schedule {
 #define SDE_FLAG_FUSED 4u        /* general coupling, tensor-core form: run the SRK2
                                     sub-steps in the GEMM epilogue instead of as
                                     separate kernels (same results bit for bit) */
+#define SDE_FLAG_EULER 8u        /* Euler-Maruyama instead of SRK2 (Alg. 2): the
+                                    first-order scheme of PROG2 (Sec. 4.2).
+                                    Josephson: every schedule, same kernels with
+                                    the one-stage step.  Kuramoto pairwise: PROG2's
+                                    two kernels per step, UpdateRHS (the tiled
+                                    all-pairs sum of Alg. 3, stored) then
+                                    AdvanceSystem (phi += dt drift + noise).  Other
+                                    Kuramoto models: SDE_ERR_UNSUPPORTED */
 
 /* One parameter point of Eq. 1. */
 typedef struct sde_jj_point {

@@ -225,8 +225,10 @@ sde_status jj_autotune(sde_ctx *c) {
     il.push_back(1);  // the per-path kernel of Alg. 1: one thread per path
   else
     il = {1, 2, 11, 12};
+  // Euler-Maruyama kernels carry the variant code + 100
+  const int scheme = (c->cfg.flags & SDE_FLAG_EULER) ? 100 : 0;
   for (int b : bl)
-    for (int i : il) cand.push_back({b, i});
+    for (int i : il) cand.push_back({b, i + scheme});
   if (cand.size() == 1) {
     c->block = cand[0].first;
     c->ilp = cand[0].second;
@@ -522,7 +524,7 @@ sde_status sde_get_tuning(const sde_ctx *c, int32_t *block, int32_t *ilp, int32_
     return SDE_OK;
   }
   if (block) *block = c->block;
-  if (ilp) *ilp = c->ilp;
+  if (ilp) *ilp = c->ilp % 100;
   if (cluster) *cluster = 1;
   return SDE_OK;
 }

@@ -55,15 +55,23 @@ __device__ __forceinline__ float cos2pi(float x) {
   return b * p;
 }
 
-// One SRK2 step.  x is kept in [0, 1) up to the drift of the steps since the
-// last wrap (at most four steps, see jj_segment).
-// e0, e1: the drive and bias a cos(omega t) + f at t_n and t_{n+1}.
-template <bool ACC>
+// One SRK2 step (Alg. 2), or with EM one Euler-Maruyama step (the
+// first-order scheme of PROG2, Sec. 4.2).  x is kept in [0, 1) up to the
+// drift of the steps since the last wrap (at most four steps, see
+// jj_segment).  e0, e1: the drive and bias a cos(omega t) + f at t_n and
+// t_{n+1}.
+template <bool ACC, bool EM>
 __device__ __forceinline__ void jj_step(float &x, float &v, float &acc, float z, const JJConsts &c, float e0,
                                         float e1) {
   const float nz = c.s * z;
   const float c1 = cos2pi(x);
   const float F1 = fmaf(-kTwoPiF, c1, fmaf(-c.gamma, v, e0));
+  if (EM) {
+    x = fmaf(c.dt, v, x);
+    v = fmaf(c.dt, F1, v + nz);
+    if (ACC) acc += v;
+    return;
+  }
   const float xt = fmaf(c.dt, v, x);
   const float vt = fmaf(c.dt, F1, v + nz);
   const float c2 = cos2pi(xt);
@@ -82,7 +90,7 @@ __device__ __forceinline__ void jj_wrap(float &x, int &w) {
 
 // Advance ILP paths over the steps [n0, n1).  `k` is the drive-table index
 // of step n0 (n0 mod P) and is updated.
-template <int ILP, bool ACC>
+template <int ILP, bool ACC, bool EM = false>
 __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float (&v)[ILP],
                                            double (&vs)[ILP], const JJConsts &c,
                                            const float *__restrict__ drive, int P, int &k,
@@ -122,7 +130,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
 #pragma unroll
       for (int s = 0; s < 4; ++s)
 #pragma unroll
-        for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, e[s], e[s + 1]);
+        for (int i = 0; i < ILP; ++i) jj_step<ACC, EM>(x[i], v[i], acc[i], z[i][s], c, e[s], e[s + 1]);
     } else {
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
@@ -132,7 +140,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
           k = (k + 1 == P) ? 0 : k + 1;
           const float e1 = fmaf(c.a, drive[k], c.f);
 #pragma unroll
-          for (int i = 0; i < ILP; ++i) jj_step<ACC>(x[i], v[i], acc[i], z[i][s], c, e0, e1);
+          for (int i = 0; i < ILP; ++i) jj_step<ACC, EM>(x[i], v[i], acc[i], z[i][s], c, e0, e1);
         }
       }
     }
@@ -160,7 +168,7 @@ __device__ __forceinline__ double warp_sum(double a) {
   return a;
 }
 
-template <int ILP>
+template <int ILP, bool EM>
 __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, int lane) {
   const JJUnit un = A.units[u];
   const JJConsts c = A.consts[un.point];
@@ -196,8 +204,8 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
   if (nb < ne) {
     int k = (int)(nb % A.P);
     const int64_t split = ne < c.wstart ? ne : c.wstart;
-    jj_segment<ILP, false>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point);
-    jj_segment<ILP, true>(x, w, v, vs, c, drive, A.P, k, nb > c.wstart ? nb : c.wstart, ne, key, pid,
+    jj_segment<ILP, false, EM>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point);
+    jj_segment<ILP, true, EM>(x, w, v, vs, c, drive, A.P, k, nb > c.wstart ? nb : c.wstart, ne, key, pid,
                           (uint32_t)un.point);
   }
   bool bad = false;
@@ -241,7 +249,7 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
   if (lane == 0) A.partials[u] = Moments{cnt, mean, m2};
 }
 
-template <int ILP>
+template <int ILP, bool EM>
 __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
   // drive table cos(2 pi k / P), k = 0 .. P + 3 (four entries of padding
   // repeat the start of the period), 16-byte aligned
@@ -258,25 +266,25 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
       if (lane == 0) u = (int)atomicAdd(A.queue, 1u) + A.unit_begin;
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= A.unit_end) break;
-      jj_unit<ILP>(A, u, drive_s, lane);
+      jj_unit<ILP, EM>(A, u, drive_s, lane);
     }
   } else {
     const int u = A.unit_begin + blockIdx.x * warps + (threadIdx.x >> 5);
-    if (u < A.unit_end) jj_unit<ILP>(A, u, drive_s, lane);
+    if (u < A.unit_end) jj_unit<ILP, EM>(A, u, drive_s, lane);
   }
 }
 
-template <int ILP>
+template <int ILP, bool EM = false>
 __global__ void __launch_bounds__(512) jj_kernel(const JJLaunchArgs A) {
-  jj_kernel_body<ILP>(A);
+  jj_kernel_body<ILP, EM>(A);
 }
 
 // The same kernel with registers capped at 64 per thread (blocks of up to 512
 // threads, two per SM): more resident warps for more spills; the autotuner
 // picks.
-template <int ILP>
+template <int ILP, bool EM = false>
 __global__ void __launch_bounds__(512, 2) jj_kernel_cap64(const JJLaunchArgs A) {
-  jj_kernel_body<ILP>(A);
+  jj_kernel_body<ILP, EM>(A);
 }
 
 __global__ void jj_prepare_kernel(const sde_jj_point *pts, int n_points, int P,
@@ -366,6 +374,10 @@ void *jj_kernel_ptr(int variant) {
     case 2: return (void *)jj_kernel<2>;
     case 11: return (void *)jj_kernel_cap64<1>;
     case 12: return (void *)jj_kernel_cap64<2>;
+    case 101: return (void *)jj_kernel<1, true>;
+    case 102: return (void *)jj_kernel<2, true>;
+    case 111: return (void *)jj_kernel_cap64<1, true>;
+    case 112: return (void *)jj_kernel_cap64<2, true>;
   }
   return nullptr;
 }
@@ -389,6 +401,11 @@ cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaS
     case 2: jj_kernel<2><<<grid, block, smem, s>>>(a); break;
     case 11: jj_kernel_cap64<1><<<grid, block, smem, s>>>(a); break;
     case 12: jj_kernel_cap64<2><<<grid, block, smem, s>>>(a); break;
+    // Euler-Maruyama variants: the code + 100
+    case 101: jj_kernel<1, true><<<grid, block, smem, s>>>(a); break;
+    case 102: jj_kernel<2, true><<<grid, block, smem, s>>>(a); break;
+    case 111: jj_kernel_cap64<1, true><<<grid, block, smem, s>>>(a); break;
+    case 112: jj_kernel_cap64<2, true><<<grid, block, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -468,14 +468,16 @@ constexpr int kPairTile = kPairThreads * kPairPerThread;
 // One SRK2 stage: receivers i of one replica in this CTA, all sources j
 // streamed through shared memory in tiles.  STAGE 0 (predictor) reads the
 // phases theta, writes theta~ and the first-stage coupling sum g1; STAGE 1
-// (corrector) takes the sums over theta~ and writes the new theta.
+// (corrector) takes the sums over theta~ and writes the new theta.  STAGE 2
+// is PROG2's UpdateRHS: the sums over theta, stored in g1 for the
+// AdvanceSystem kernel of the Euler-Maruyama scheme.
 template <int STAGE>
 __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPairArgs A) {
   __shared__ float src_s[kPairTile];
   const int rep = blockIdx.y;
   const int64_t N = A.N;
   const int64_t base = (int64_t)rep * N;
-  const uint32_t *src = STAGE == 0 ? A.theta : A.theta_t;
+  const uint32_t *src = STAGE == 1 ? A.theta_t : A.theta;  // corrector: sums over theta~
   float ti[kPairPerThread], acc[kPairPerThread];
   int64_t idx[kPairPerThread];
 #pragma unroll
@@ -508,6 +510,12 @@ __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPair
     }
     __syncthreads();
   }
+  if (STAGE == 2) {
+#pragma unroll
+    for (int k = 0; k < kPairPerThread; ++k)
+      if (idx[k] < N) A.g1[base + idx[k]] = acc[k];
+    return;
+  }
   const uint2 key = seed_to_key(A.seed);
   const int64_t n = A.n;
 #pragma unroll
@@ -526,6 +534,21 @@ __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPair
       const float d = fmaf(A.sc, psi, fmaf(A.kh, A.g1[gi] + acc[k], wdt));
       A.theta[gi] += (uint32_t)__float2int_rn(d * 4294967296.0f);
     }
+  }
+}
+
+// PROG2's AdvanceSystem with Euler-Maruyama: theta += wdt + kc g + sc psi
+// for every oscillator of every replica, g the stored coupling sums.
+__global__ void kur_advance_euler_kernel(const KurPairArgs A, int64_t R) {
+  const uint2 key = seed_to_key(A.seed);
+  const int64_t NR = A.N * R;
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < NR;
+       gi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rep = gi / A.N, i = gi - rep * A.N;
+    float z[4];
+    gauss4((uint32_t)(A.n >> 2), (uint32_t)i, (uint32_t)rep, kTagKuramoto, key, z);
+    const float d = fmaf(A.sc, pick4(z, (int)(A.n & 3)), fmaf(A.kc, A.g1[gi], A.omega[gi] * A.wscale));
+    A.theta[gi] += (uint32_t)__float2int_rn(d * 4294967296.0f);
   }
 }
 
@@ -875,6 +898,13 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   SDE_CHECK_ARG(cfg->dt > 0.0, "dt must be > 0");
   SDE_CHECK_ARG(cfg->sample_every >= 0, "sample_every must be >= 0");
   SDE_CHECK_ARG(cfg->n_osc < (1ll << 31), "n_osc too large");
+  if (cfg->flags & SDE_FLAG_EULER) {
+    if (cfg->model != SDE_KURAMOTO_PAIRWISE) {
+      set_error("unsupported: Euler-Maruyama (SDE_FLAG_EULER) is built for the Josephson and the "
+                "pairwise Kuramoto models");
+      return SDE_ERR_UNSUPPORTED;
+    }
+  }
   const bool mf = cfg->model == SDE_KURAMOTO_MEANFIELD;
   if (mf)
     SDE_CHECK_ARG(cfg->schedule == SDE_SCHED_PERSISTENT || cfg->schedule == SDE_SCHED_GRID,
@@ -1092,12 +1122,23 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
     a.seed = k->seed;
     const dim3 grid((unsigned)((k->N + kPairTile - 1) / kPairTile), (unsigned)k->R);
     int64_t sample = 0;
+    const bool euler = (k->flags & SDE_FLAG_EULER) != 0;
+    const int64_t NR = k->N * k->R;
+    const unsigned adv_grid = (unsigned)std::min<int64_t>((NR + 255) / 256, (int64_t)k->sm_count * 8);
     for (int64_t n = r->n_begin; n < r->n_end; ++n) {
       if (k->M > 0 && (n - r->n_begin) % k->M == 0) {
         kur_order_kernel<<<(unsigned)k->R, 256, 0, s>>>(k->theta, k->N, k->R, rbuf + sample * k->R);
         ++sample;
       }
       a.n = n;
+      if (euler) {
+        // PROG2: UpdateRHS, then AdvanceSystem
+        SDE_CUDA_TRY(ktime_begin(k, s));
+        kur_pairwise_stage<2><<<grid, kPairThreads, 0, s>>>(a);
+        SDE_CUDA_TRY(ktime_end(k, s));
+        kur_advance_euler_kernel<<<adv_grid, 256, 0, s>>>(a, k->R);
+        continue;
+      }
       SDE_CUDA_TRY(ktime_begin(k, s));
       kur_pairwise_stage<0><<<grid, kPairThreads, 0, s>>>(a);
       SDE_CUDA_TRY(ktime_end(k, s));

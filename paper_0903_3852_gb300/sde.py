@@ -14,6 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libsde_gb300.so")
 
 SDE_OK = 0
+SDE_ERR_INVALID_ARG, SDE_ERR_CUDA, SDE_ERR_NO_MEMORY, SDE_ERR_TIMEOUT, SDE_ERR_UNSUPPORTED, SDE_ERR_NUMERIC = 1, 2, 3, 4, 5, 6
 STATUS_NAMES = {0: "SDE_OK", 1: "SDE_ERR_INVALID_ARG", 2: "SDE_ERR_CUDA", 3: "SDE_ERR_NO_MEMORY",
                 4: "SDE_ERR_TIMEOUT", 5: "SDE_ERR_UNSUPPORTED", 6: "SDE_ERR_NUMERIC"}
 
@@ -30,6 +31,7 @@ SDE_SCHED_GRID = 2
 SDE_FLAG_NO_GRAPH = 1
 SDE_FLAG_TIME_KERNELS = 2
 SDE_FLAG_FUSED = 4
+SDE_FLAG_EULER = 8
 
 
 class SDEError(RuntimeError):
