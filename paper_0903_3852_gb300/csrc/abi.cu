@@ -310,8 +310,9 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
                     (cfg->block_threads >= 32 && cfg->block_threads <= 512 &&
                      cfg->block_threads % 32 == 0),
                 "block_threads must be 0 or a multiple of 32 in [32, 512]");
-  SDE_CHECK_ARG(cfg->paths_per_thread >= 0 && cfg->paths_per_thread <= 2,
-                "paths_per_thread must be 0, 1 or 2");
+  SDE_CHECK_ARG(cfg->paths_per_thread == 0 || cfg->paths_per_thread == 1 || cfg->paths_per_thread == 2 ||
+                    cfg->paths_per_thread == 11 || cfg->paths_per_thread == 12,
+                "paths_per_thread must be 0, 1, 2, 11 or 12");
   c->n_points = cfg->n_points;
   c->P = cfg->steps_per_period;
   c->paths.resize(c->n_points);

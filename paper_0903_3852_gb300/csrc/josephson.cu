@@ -16,7 +16,7 @@
 // memory.  Position is kept as x in [0, 1) plus an integer winding count
 // (folded once per group of four steps), so FP32 resolution does not degrade
 // as paths run away.  cos(2 pi x) is a branch-free minimax polynomial
-// (cos2pi below).
+// (jj_force below).
 //
 // The window average of v (the time-averaged velocity <<v>> of Sec. 5) is
 // summed in FP32 over blocks of 64 steps (aligned to absolute step indices)
@@ -34,25 +34,24 @@
 namespace sde {
 namespace {
 
-constexpr float kTwoPiF = 6.28318530717958647692f;
 
-// cos(2 pi x) for |x| < 2^22 without branches: with r = x - rint(x) in
-// [-1/2, 1/2] and b = 1/4 - |r| in [-1/4, 1/4], cos(2 pi x) = sin(2 pi b),
+// A - 2 pi cos(2 pi x) for |x| < 2^22 without branches: with r = x - rint(x)
+// in [-1/2, 1/2] and b = 1/4 - |r| in [-1/4, 1/4], cos(2 pi x) = sin(2 pi b),
 // and sin(2 pi b) = b P(b^2) with P a degree-4 polynomial whose coefficients
 // minimise the largest absolute error on [0, 1/4] (Lawson's iteratively
-// reweighted least squares, about 3e-9 in exact arithmetic).  In FP32 the
-// error is at most 1.7e-7 (RMS 3.7e-8).  rint comes from adding and
-// subtracting 1.5 * 2^23, all on the FMA pipe.
-__device__ __forceinline__ float cos2pi(float x) {
-  const float t = (x + 12582912.0f) - 12582912.0f;
-  const float b = 0.25f - fabsf(x - t);
+// reweighted least squares, about 3e-9 in exact arithmetic).  The factor
+// -2 pi of Eq. 1's force is folded into P, so the force term and the addend
+// A = a cos(omega t) + f - gamma v cost one FMA.  In FP32 the error of
+// cos(2 pi x) is at most 1.7e-7 (RMS 3.7e-8).
+__device__ __forceinline__ float jj_force(float x, float A) {
+  const float b = 0.25f - fabsf(x - rintf(x));
   const float s = b * b;
-  float p = 39.536705f;
-  p = fmaf(p, s, -76.5497818f);
-  p = fmaf(p, s, 81.6010056f);
-  p = fmaf(p, s, -41.3416557f);
-  p = fmaf(p, s, 6.28318501f);
-  return b * p;
+  float p = -2.484164429e+02f;  // -2 pi x (39.536705, -76.5497818, 81.6010056, -41.3416557, 6.28318501)
+  p = fmaf(p, s, 4.809764709e+02f);
+  p = fmaf(p, s, -5.127142334e+02f);
+  p = fmaf(p, s, 2.597572937e+02f);
+  p = fmaf(p, s, -3.947841644e+01f);
+  return fmaf(b, p, A);
 }
 
 // One SRK2 step (Alg. 2), or with EM one Euler-Maruyama step (the
@@ -63,21 +62,19 @@ __device__ __forceinline__ float cos2pi(float x) {
 template <bool ACC, bool EM>
 __device__ __forceinline__ void jj_step(float &x, float &v, float &acc, float z, const JJConsts &c, float e0,
                                         float e1) {
-  const float nz = c.s * z;
-  const float c1 = cos2pi(x);
-  const float F1 = fmaf(-kTwoPiF, c1, fmaf(-c.gamma, v, e0));
+  const float vn = fmaf(c.s, z, v);  // v plus the noise increment, used by both stages
+  const float F1 = jj_force(x, fmaf(-c.gamma, v, e0));
   if (EM) {
     x = fmaf(c.dt, v, x);
-    v = fmaf(c.dt, F1, v + nz);
+    v = fmaf(c.dt, F1, vn);
     if (ACC) acc += v;
     return;
   }
   const float xt = fmaf(c.dt, v, x);
-  const float vt = fmaf(c.dt, F1, v + nz);
-  const float c2 = cos2pi(xt);
-  const float F2 = fmaf(-kTwoPiF, c2, fmaf(-c.gamma, vt, e1));
+  const float vt = fmaf(c.dt, F1, vn);
+  const float F2 = jj_force(xt, fmaf(-c.gamma, vt, e1));
   x = fmaf(c.h, v + vt, x);
-  v = fmaf(c.h, F1 + F2, v + nz);
+  v = fmaf(c.h, F1 + F2, vn);
   if (ACC) acc += v;
 }
 
@@ -95,7 +92,8 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
                                            double (&vs)[ILP], const JJConsts &c,
                                            const float *__restrict__ drive, int P, int &k,
                                            int64_t n0, int64_t n1, const PhiloxKeys &key,
-                                           const uint32_t (&pid)[ILP], uint32_t point) {
+                                           const uint32_t (&pid)[ILP], uint32_t point,
+                                           const float2 *bm_tab) {
   if (n0 >= n1) return;
   float acc[ILP];
 #pragma unroll
@@ -105,7 +103,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
   for (uint32_t g = g0; g <= g1; ++g) {
     float z[ILP][4];
 #pragma unroll
-    for (int i = 0; i < ILP; ++i) gauss4(g, pid[i], point, kTagJosephson, key, z[i]);
+    for (int i = 0; i < ILP; ++i) gauss4_tab(g, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
     const int64_t base = (int64_t)g << 2;
     if (base >= n0 && base + 4 <= n1) {
       // full group: drive values at t_{4g} .. t_{4g+4}
@@ -169,7 +167,8 @@ __device__ __forceinline__ double warp_sum(double a) {
 }
 
 template <int ILP, bool EM>
-__device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, int lane) {
+__device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, const float2 *bm_tab,
+                                        int lane) {
   const JJUnit un = A.units[u];
   const JJConsts c = A.consts[un.point];
   const PhiloxKeys &key = A.keys;
@@ -204,9 +203,9 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
   if (nb < ne) {
     int k = (int)(nb % A.P);
     const int64_t split = ne < c.wstart ? ne : c.wstart;
-    jj_segment<ILP, false, EM>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point);
+    jj_segment<ILP, false, EM>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point, bm_tab);
     jj_segment<ILP, true, EM>(x, w, v, vs, c, drive, A.P, k, nb > c.wstart ? nb : c.wstart, ne, key, pid,
-                          (uint32_t)un.point);
+                              (uint32_t)un.point, bm_tab);
   }
   bool bad = false;
 #pragma unroll
@@ -254,8 +253,10 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
   // drive table cos(2 pi k / P), k = 0 .. P + 3 (four entries of padding
   // repeat the start of the period), 16-byte aligned
   extern __shared__ float4 drive_s4[];
+  __shared__ float2 bm_tab[256];  // Box-Muller angle table
   float *drive_s = reinterpret_cast<float *>(drive_s4);
   for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x) drive_s[i] = A.drive[i % A.P];
+  fill_bm_table(bm_tab);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
@@ -266,11 +267,11 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
       if (lane == 0) u = (int)atomicAdd(A.queue, 1u) + A.unit_begin;
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= A.unit_end) break;
-      jj_unit<ILP, EM>(A, u, drive_s, lane);
+      jj_unit<ILP, EM>(A, u, drive_s, bm_tab, lane);
     }
   } else {
     const int u = A.unit_begin + blockIdx.x * warps + (threadIdx.x >> 5);
-    if (u < A.unit_end) jj_unit<ILP, EM>(A, u, drive_s, lane);
+    if (u < A.unit_end) jj_unit<ILP, EM>(A, u, drive_s, bm_tab, lane);
   }
 }
 
@@ -483,10 +484,12 @@ struct NoallocArgs {
 // unit decomposition as the plain schedule with one path per thread.
 __global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
   extern __shared__ float4 drive_s4[];
+  __shared__ float2 bm_tab[256];
   float *drive_s = reinterpret_cast<float *>(drive_s4);
   const double dt = 2.0 * 3.14159265358979323846 / (A.p.omega * (double)A.P);
   for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x)
     drive_s[i] = (float)cospi(2.0 * (double)(i % A.P) / (double)A.P);
+  fill_bm_table(bm_tab);
   __syncthreads();
   JJConsts c;
   c.gamma = (float)A.p.gamma;
@@ -525,9 +528,9 @@ __global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
   if (A.n_begin < ne) {
     int k = (int)(A.n_begin % A.P);
     const int64_t split = ne < c.wstart ? ne : c.wstart;
-    jj_segment<1, false>(x, w, v, vs, c, drive_s, A.P, k, A.n_begin, split, key, pid, 0u);
+    jj_segment<1, false>(x, w, v, vs, c, drive_s, A.P, k, A.n_begin, split, key, pid, 0u, bm_tab);
     jj_segment<1, true>(x, w, v, vs, c, drive_s, A.P, k, A.n_begin > c.wstart ? A.n_begin : c.wstart, ne,
-                        key, pid, 0u);
+                        key, pid, 0u, bm_tab);
   }
   if (valid) {
     A.st.x_out[j] = x[0];

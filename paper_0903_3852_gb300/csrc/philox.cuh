@@ -22,14 +22,15 @@
 
 namespace sde {
 
+// Each round's two 32 x 32 -> 64-bit products are written as 64-bit
+// multiplies, one wide multiply-add instruction each.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;
+    const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y,
+                   (uint32_t)p0);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
   }
@@ -58,11 +59,10 @@ __host__ __device__ inline PhiloxKeys philox_round_keys(uint64_t seed) {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &K) {
 #pragma unroll
   for (int round = 0; round < 10; ++round) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ K.k[2 * round], lo1, hi0 ^ c.w ^ K.k[2 * round + 1], lo0);
+    const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;
+    const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k[2 * round], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ K.k[2 * round + 1], (uint32_t)p0);
   }
   return c;
 }
@@ -75,12 +75,17 @@ __device__ __forceinline__ float uniform24(uint32_t w) {
   return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;  // 2^-24
 }
 
+// sqrt(L) for the Box-Muller radius by the hardware square-root
+// approximation (one instruction; L = 0, reached when u0 = 1, gives 0).
+__device__ __forceinline__ float radius(float L) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(L));
+  return r;
+}
+
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float &z0, float &z1) {
   const float u0 = uniform24(w0);
-  // sqrt(L) as L rsqrt(L) (two instructions, within 2 ulp); L = 0 exactly
-  // when u0 = 1, which 1 in 2^24 draws hit
-  const float L = -2.0f * logf(u0);
-  const float rho = L > 0.0f ? L * rsqrtf(L) : 0.0f;
+  const float rho = radius(-2.0f * logf(u0));
   float s, c;
   sincos_turns(((w1 >> 8) + 1u) << 8, s, c);
   z0 = rho * c;
@@ -122,6 +127,43 @@ __device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uin
   float z0, z1;
   box_muller(hi ? r.z : r.x, hi ? r.w : r.y, z0, z1);
   return (n & 1) ? z1 : z0;
+}
+
+// Box-Muller with the angle's sine and cosine from a table: the angle
+// 2 pi u1, u1 = (j + 1) 2^-24 with j = w1 >> 8, is split into the table
+// angle 2 pi q / 256 (q = the top 8 bits of j) and a remainder
+// b = 2 pi ((j mod 2^16) + 1) 2^-24 in (0, 2 pi / 256]; sin b = b - b^3/6 and
+// cos b = 1 - b^2/2 (the next terms are below 1.5e-8), and the angle-addition
+// formulas combine them with the table entry.  Same values as box_muller to
+// about 1e-7.  tab[q] = (cos, sin)(2 pi q / 256), q = 0 .. 255, filled by
+// fill_bm_table (shared memory of the calling kernel).
+__device__ __forceinline__ void fill_bm_table(float2 *tab) {
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+    float sn, cs;
+    sincospif((float)q * 0.0078125f, &sn, &cs);  // q / 128
+    tab[q] = make_float2(cs, sn);
+  }
+}
+
+__device__ __forceinline__ void box_muller_tab(uint32_t w0, uint32_t w1, const float2 *tab, float &z0,
+                                               float &z1) {
+  const float u0 = fmaf((float)(w0 >> 8), 5.9604644775390625e-8f, 5.9604644775390625e-8f);  // exact
+  const float rho = radius(-2.0f * logf(u0));
+  const float2 t = tab[w1 >> 24];
+  const float b = fmaf((float)((w1 >> 8) & 0xFFFFu), 3.7450702829239308e-7f, 3.7450702829239308e-7f);  // 2 pi 2^-24
+  const float b2 = b * b;
+  const float cb = fmaf(-0.5f, b2, 1.0f);
+  const float sb = fmaf(b * b2, -0.16666667f, b);
+  z0 = rho * fmaf(t.x, cb, -t.y * sb);
+  z1 = rho * fmaf(t.y, cb, t.x * sb);
+}
+
+// gauss4 with round keys and the Box-Muller angle table.
+__device__ __forceinline__ void gauss4_tab(uint32_t g, uint32_t c1, uint32_t c2, uint32_t tag,
+                                           const PhiloxKeys &K, const float2 *tab, float (&z)[4]) {
+  const uint4 r = philox4x32_10(make_uint4(g, c1, c2, tag), K);
+  box_muller_tab(r.x, r.y, tab, z[0], z[1]);
+  box_muller_tab(r.z, r.w, tab, z[2], z[3]);
 }
 
 // Element k (0..3) of a 4-vector without dynamic register indexing.
