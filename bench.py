@@ -309,7 +309,9 @@ def run_ours(args, rank, world, device):
             units = float(w["n_osc"] * w["replicas"] * S)
             metric = "oscillator-steps/sec"
             launches_per_step = 2 * S + 4
-            bytes_per_launch = 16.0 * w["n_osc"] * w["replicas"]  # read 8-12 B, write 4-8 B per oscillator
+            # 152 B per oscillator per 4 steps (noise-drawing predictor 28, predictor 20
+            # three times, corrector 16 four times): 19 B per launch on average
+            bytes_per_launch = 19.0 * w["n_osc"] * w["replicas"]
         elif model == sde.SDE_KURAMOTO_MEANFIELD:
             units = float(w["n_osc"] * w["replicas"] * S)
             metric = "oscillator-steps/sec"
@@ -428,7 +430,7 @@ def run_ours(args, rank, world, device):
     if args.workload == "kuramoto-fig4":
         bound, peak = "hbm", peaks["hbm_gbs"]
         peak_note = "HBM copy bandwidth, %s" % peak_src
-        flop_note = "16 B per oscillator per stage launch (theta, omega or theta~, y read; theta~, y or theta written)"
+        flop_note = "19 B per oscillator per launch (38 B per oscillator-step over the predictor and corrector launches)"
     elif args.workload == "fig2-fp64":
         bound, peak = "alu", fp64_peak_tflops(props)
         peak_note = "%d SM x 2 DFMA x 2 FLOP x 2070 MHz (derived)" % props.multi_processor_count
@@ -451,9 +453,18 @@ def run_ours(args, rank, world, device):
     # DRAM bytes per launch of the dominant kernel from the ncu captures
     # summarised under profiles/ (null where the kernel changed since)
     traffic, traffic_src = None, None
-    if args.workload in ("sweep", "plain", "fig2"):
-        traffic = 8.7 * n  # jj_kernel: 8.7 B per path (the state read once)
-        traffic_src = "profiles/jj_kernel_sweep_64pts_cap20000.md, scaled by paths"
+    if args.workload in ("sweep", "plain", "fig2") and not args.euler:
+        traffic = 8.34 * n  # jj_kernel: 8.34 B per path (the initial state read once)
+        traffic_src = "profiles/jj_kernel_sweep_512pts_cap2000.md, scaled by paths"
+    elif args.workload == "kuramoto-fig4":
+        traffic = 16.9 * w["n_osc"] * w["replicas"]  # mean over the three launch kinds of a step
+        traffic_src = "profiles/kur_mfg_kernel_fig4_N16777216.md"
+    elif args.workload == "kuramoto-general" and not args.fused:
+        traffic = 146.2e6  # tc_gemm_bf16_kernel: K (134 MB) once + operands and output
+        traffic_src = "profiles/tc_gemm_bf16_kernel_N8192_R256.md"
+    elif args.workload == "kuramoto-pairwise" and not args.euler:
+        traffic = 2.12e6
+        traffic_src = "profiles/kur_pairwise_stage_N4096_R64.md"
     res = {
         "metric": metric,
         "value": sde_dist.aggregate_rate(units, world, ms * 1e-3),
