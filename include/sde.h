@@ -290,6 +290,19 @@ sde_status sde_box_muller(const uint32_t *ctr_dev, uint64_t seed, float *z_dev, 
                           void *stream);
 
 /*
+ * The Box-Muller transform (Sec. 4.1) of given 32-bit word pairs:
+ * w_dev[2i], w_dev[2i+1] -> z_dev[2i], z_dev[2i+1] (device arrays, 8-byte
+ * aligned), with the uniforms of sde_box_muller.  variant 0: the transform
+ * the Kuramoto and surrogate kernels use (accurate logf, sin/cos of the
+ * fixed-point angle); variant 1: the Josephson kernels' (angle from a
+ * 256-entry table plus angle addition; ln u0 from the hardware base-2
+ * logarithm: the radius is within ~5e-4 absolute, and within ~1e-7
+ * relative for u0 well below 1).  For exhaustive checks of both.
+ */
+sde_status sde_box_muller_words(const uint32_t *w_dev, int64_t n_pairs, int32_t variant, float *z_dev,
+                                void *stream);
+
+/*
  * Allocation-free run of one Eq. 1 parameter point.  The paper has no
  * counterpart: this is an interface for callers that must not allocate
  * device memory -- code running inside another framework's memory pool or

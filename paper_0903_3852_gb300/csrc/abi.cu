@@ -611,4 +611,14 @@ sde_status sde_box_muller(const uint32_t *ctr, uint64_t seed, float *z, int64_t 
   return SDE_OK;
 }
 
+sde_status sde_box_muller_words(const uint32_t *w, int64_t n_pairs, int32_t variant, float *z, void *stream) {
+  clear_error();
+  SDE_CHECK_ARG(n_pairs >= 0, "n_pairs must be >= 0");
+  SDE_CHECK_ARG(variant == 0 || variant == 1, "variant must be 0 or 1");
+  SDE_CHECK_ARG(n_pairs == 0 || (w && z), "w and z must be non-NULL");
+  SDE_CHECK_ARG(((uintptr_t)w % 8) == 0 && ((uintptr_t)z % 8) == 0, "w and z must be 8-byte aligned");
+  SDE_CUDA_TRY(box_muller_words(w, n_pairs, variant, z, (cudaStream_t)stream));
+  return SDE_OK;
+}
+
 }  // extern "C"

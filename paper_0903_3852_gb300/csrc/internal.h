@@ -94,5 +94,6 @@ cudaError_t phase_hist(const float *phi, int64_t n, int32_t nbins, unsigned long
 
 cudaError_t philox_fill(const uint32_t *ctr, uint64_t seed, uint32_t *out, int64_t n, cudaStream_t s);
 cudaError_t box_muller_fill(const uint32_t *ctr, uint64_t seed, float *z, int64_t n, cudaStream_t s);
+cudaError_t box_muller_words(const uint32_t *w, int64_t n, int variant, float *z, cudaStream_t s);
 
 }  // namespace sde

@@ -369,6 +369,25 @@ __global__ void box_muller_fill_kernel(const uint4 *ctr, uint2 key, float4 *z, i
   }
 }
 
+// Box-Muller of given word pairs (w0, w1) -> (z0, z1): variant 0 the
+// library's default transform, 1 the Josephson kernels' (table angle,
+// hardware logarithm).
+__global__ void box_muller_words_kernel(const uint2 *w, int64_t n, int variant, float2 *z) {
+  __shared__ float2 tab[256];
+  fill_bm_table(tab);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 p = w[i];
+    float2 o;
+    if (variant == 1)
+      box_muller_tab(p.x, p.y, tab, o.x, o.y);
+    else
+      box_muller(p.x, p.y, o.x, o.y);
+    z[i] = o;
+  }
+}
+
 void *jj_kernel_ptr(int variant) {
   switch (variant) {
     case 1: return (void *)jj_kernel<1>;
@@ -442,6 +461,14 @@ cudaError_t box_muller_fill(const uint32_t *ctr, uint64_t seed, float *z, int64_
   const int64_t blocks = (n + 255) / 256;
   box_muller_fill_kernel<<<(int)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(
       (const uint4 *)ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)), (float4 *)z, n);
+  return cudaGetLastError();
+}
+
+cudaError_t box_muller_words(const uint32_t *w, int64_t n, int variant, float *z, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  box_muller_words_kernel<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>((const uint2 *)w, n, variant,
+                                                                               (float2 *)z);
   return cudaGetLastError();
 }
 

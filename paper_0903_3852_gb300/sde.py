@@ -115,6 +115,7 @@ SIGNATURES = [
     ("sde_josephson_run_noalloc", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_int64, ctypes.c_int64] + [_VP] * 9 + [_VP]),
+    ("sde_box_muller_words", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
     ("sde_josephson_run_fp64", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64] + [_VP] * 7 + [_VP]),
@@ -327,6 +328,17 @@ def josephson_run_noalloc(point, steps_per_period, n_paths, total_steps, seed, n
         ctypes.byref(p), steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
         _ptr(x_in), _ptr(v_in), _ptr(w_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(w_out),
         _ptr(vsum_out), _ptr(obs_out), _stream(stream)))
+
+
+def box_muller_words(w, variant=0, stream=None):
+    """sde_box_muller_words: Gaussians from given word pairs; w is a CUDA int32/uint32
+    tensor of shape (n, 2); returns a float32 tensor (n, 2)."""
+    import torch
+    assert w.is_cuda and w.dim() == 2 and w.shape[1] == 2 and w.element_size() == 4
+    w = w.contiguous()
+    z = torch.empty(w.shape, dtype=torch.float32, device=w.device)
+    _check(lib().sde_box_muller_words(_ptr(w), w.shape[0], variant, _ptr(z), _stream(stream)))
+    return z
 
 
 def josephson_run_fp64(point, steps_per_period, total_steps, seed, n_begin, n_end, x_in, v_in, x_out, v_out,

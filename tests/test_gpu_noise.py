@@ -73,3 +73,49 @@ def test_box_muller_matches_oracle():
     g = [oracle.gaussian(seed, int(c[1, 3]), int(c[1, 1]), int(c[1, 2]), 4 * int(c[1, 0]) + k)
          for k in range(4)]
     assert np.allclose(z[1], g, rtol=6e-7, atol=2e-7)
+
+
+def _bm_ref(w0, w1):
+    u0 = ((w0.astype(np.uint64) >> 8) + 1).astype(np.float64) * 2.0 ** -24
+    u1 = ((w1.astype(np.uint64) >> 8) + 1).astype(np.float64) * 2.0 ** -24
+    rho = np.sqrt(-2.0 * np.log(u0))
+    return rho * np.cos(2 * np.pi * u1), rho * np.sin(2 * np.pi * u1), u0
+
+
+def test_box_muller_words_both_variants_against_fp64():
+    ensure_built()
+    rng = np.random.default_rng(12)
+    w = rng.integers(0, 2 ** 32, size=(400_000, 2), dtype=np.uint64).astype(np.uint32)
+    wt = torch.from_numpy(w.view(np.int32)).cuda()
+    r0, r1, u0 = _bm_ref(w[:, 0], w[:, 1])
+    ref = np.stack([r0, r1], 1)
+    z0 = sde.box_muller_words(wt, 0).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(z0 - ref) <= 6e-7 * np.abs(ref) + 2e-7), np.abs(z0 - ref).max()
+    z1 = sde.box_muller_words(wt, 1).cpu().numpy().astype(np.float64)
+    err = np.abs(z1 - ref)
+    far = u0 <= 0.5  # radius >= 1.18: the hardware logarithm's absolute error is relatively small
+    print("table + hardware-log variant: max err %.2e overall, %.2e relative where u0 <= 0.5"
+          % (err.max(), (err[far] / np.maximum(np.abs(ref[far]), 1e-3)).max()))
+    assert err.max() <= 5e-4
+    assert np.all(err[far] <= 6e-7 * np.abs(ref[far]) + 3e-7)
+    # the two variants agree to the same bounds
+    assert np.all(np.abs(z1 - z0)[far] <= 1e-6 * np.abs(ref[far]) + 5e-7)
+
+
+def test_box_muller_radius_exhaustive_over_all_uniforms():
+    # every one of the 2^24 values of u0, with u1 = 2^-24 (z0 = rho cos(2 pi 2^-24) ~ rho)
+    ensure_built()
+    j = np.arange(1 << 24, dtype=np.uint64)
+    w = np.zeros((1 << 24, 2), dtype=np.uint32)
+    w[:, 0] = (j << 8).astype(np.uint32)
+    wt = torch.from_numpy(w.view(np.int32)).cuda()
+    r0, _, u0 = _bm_ref(w[:, 0], w[:, 1])
+    for variant, bound in ((0, 1e-6), (1, 5e-4)):
+        z = sde.box_muller_words(wt, variant)[:, 0].cpu().numpy().astype(np.float64)
+        err = np.abs(z - r0)
+        print("variant %d: max radius error %.2e (at u0 = %.9f), u0 = 1 gives %.1e"
+              % (variant, err.max(), u0[err.argmax()], z[-1]))
+        assert np.all(np.isfinite(z)) and z[-1] == 0.0
+        assert err.max() <= bound
+        if variant == 0:
+            assert np.all(err <= 6e-7 * r0 + 2e-7)
