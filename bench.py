@@ -494,6 +494,113 @@ def run_ours(args, rank, world, device):
     return res, ens
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_worker_init(_):
+    import oracle
+    oracle.lib()
+    return 0
+
+
+def _oracle_jj_task(task):
+    """One oracle task in a worker process: a chunk of paths of one point."""
+    import oracle
+    pt, x0, v0, P, S, seed, k, path0 = task
+    oracle.jj_run(x0, v0, oracle.jj_params(**pt), P, 0, S, S, seed, point=k, path0=path0)
+    return float(len(x0) * S)
+
+
+def _oracle_kur_task(task):
+    """One oracle task in a worker process: one Kuramoto replica."""
+    import oracle
+    phi0, omega, D, dt, S, seed, r, Kconst, meanfield, units = task
+    oracle.kuramoto_run(phi0, omega, D, dt, 0, S, seed, r, Kconst=Kconst, meanfield=meanfield)
+    return units
+
+
+class OracleTimer:
+    """The FP64 oracle timed on all host cores: one process per core (spawn
+    context, safe after CUDA initialisation), each running the unchanged oracle
+    on disjoint paths or replicas of the workload; the sample is sized from the
+    single-core rate to take about `budget_s` seconds."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores = host_cores()
+        self.pool = None
+        if self.cores > 1:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+            self.pool.map(_oracle_worker_init, range(self.cores))
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def run(self, args, rate1, budget_s=10.0):
+        if self.pool is None:
+            return None
+        target = rate1 * self.cores * budget_s
+        if args.workload in ("sweep", "plain", "fig2", "fig2-fp64"):
+            w = {"sweep": sweep_workload, "plain": plain_workload, "fig2": fig2_workload,
+                 "fig2-fp64": fig2_workload}[args.workload](0)
+            if args.workload == "fig2-fp64":
+                w["steps"] = np.array([args.fp64_steps], dtype=np.int64)
+            offs = np.concatenate([[0], np.cumsum(w["paths"])])
+            per_step = float(np.sum(w["steps"]))  # path-steps of one path at every point
+            per_point = int(max(1, min(w["paths"].max(), round(target / per_step))))
+            tasks = []
+            for k, pt in enumerate(w["points"]):
+                n = min(per_point, int(w["paths"][k]))
+                S = int(w["steps"][k])
+                for c in range(0, n, 16):
+                    m = min(16, n - c)
+                    a = int(offs[k]) + c
+                    tasks.append((pt, w["x0"][a:a + m], w["v0"][a:a + m], w["steps_per_period"], S, w["seed"],
+                                  k, c))
+            t0 = time.perf_counter()
+            done = sum(self.pool.map(_oracle_jj_task, tasks, chunksize=1))
+            dt = time.perf_counter() - t0
+            return {"value": done / dt, "unit": "path-steps/s", "cores": self.cores, "kind": "oracle",
+                    "sample": "up to the first %d paths of each of %d points, full step counts (%.3g path-steps), "
+                              "16-path tasks over %d processes" % (per_point, len(w["points"]), done, self.cores)}
+        if args.workload in ("kuramoto-meanfield", "kuramoto-pairwise"):
+            w = inputs.kuramoto_uniform()
+            meanfield = args.workload == "kuramoto-meanfield"
+            N, R = w["n_osc"], w["replicas"]
+            per = N if meanfield else N * N
+            S = int(max(1, min(w["steps"], round(target / (per * R)))))
+            tasks = [(w["phi0"][r], w["omega"][r], w["D"], w["dt"], S, w["seed"], r, w["K"] / N, meanfield,
+                      float(per * S)) for r in range(R)]
+            t0 = time.perf_counter()
+            done = sum(self.pool.map(_oracle_kur_task, tasks, chunksize=1))
+            dt = time.perf_counter() - t0
+            return {"value": done / dt, "unit": "oscillator-steps/s" if meanfield else "pair-terms/s",
+                    "cores": self.cores, "kind": "oracle",
+                    "sample": "all %d replicas, %d steps each, over %d processes" % (R, S, self.cores)}
+        return None  # a single replica (Fig. 4) or the 512 MB K matrix per process: single core only
+
+
+def cpu_baseline_both(args, budget_s=20.0):
+    """Single-core oracle rate, and the all-core rate where the workload splits."""
+    one = cpu_baseline(args, budget_s=budget_s)
+    timer = OracleTimer()
+    try:
+        allc = timer.run(args, one["value"], budget_s=budget_s / 2)
+    finally:
+        timer.close()
+    if allc is None:
+        return one
+    allc["single_core"] = one
+    return allc
+
+
 def cpu_baseline(args, budget_s=20.0):
     """The FP64 oracle as it stands, on a bounded sample of the workload."""
     import oracle
@@ -563,13 +670,21 @@ def run_reference(args):
     if rank != 0:
         return None
     per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        cpu_baseline(args, budget_s=min(per, 3.0))
-    vals = []
-    last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(args, budget_s=per)
-        vals.append(last["value"])
+    one = cpu_baseline(args, budget_s=min(per, 5.0))  # the single-core rate sizes the samples
+    timer = OracleTimer()
+    try:
+        def step(budget):
+            r = timer.run(args, one["value"], budget_s=budget)
+            return r if r is not None else cpu_baseline(args, budget_s=budget)
+        for _ in range(args.warmup):
+            step(min(per, 3.0))
+        vals = []
+        last = None
+        for _ in range(args.steps):
+            last = step(per)
+            vals.append(last["value"])
+    finally:
+        timer.close()
     v = statistics.mean(vals)
     metric = {"sweep": "path-steps/sec", "plain": "path-steps/sec", "fig2": "path-steps/sec",
               "fig2-fp64": "path-steps/sec",
@@ -582,7 +697,8 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; inputs.py)",
            "config": {"workload": args.workload, "sample": last["sample"]},
-           "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": last["sample"]},
+           "cpu_baseline": {"value": v, "unit": unit, "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"], "single_core": one},
            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return res
 
@@ -692,10 +808,8 @@ def main():
         return
     res, ens = run_ours(args, rank, world, local)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
-            res["cpu_baseline"] = cpu_baseline(args)
-        elif not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(args)
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline_both(args)
         print(json.dumps(res))
     ens.close()
     if world > 1:
