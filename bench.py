@@ -51,6 +51,9 @@ def parse():
                     help="steps per bench step of the pairwise Kuramoto workload")
     ap.add_argument("--fig4-steps", type=int, default=None,
                     help="kuramoto-fig4: steps per bench step (default: the workload's 2000)")
+    ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto",
+                    help="Josephson workloads: persistent sweep launch (default except 'plain') or one "
+                         "launch per point with one thread per path (the plain per-path kernel)")
     ap.add_argument("--euler", action="store_true",
                     help="Euler-Maruyama (PROG2's scheme) instead of SRK2: Josephson workloads and kuramoto-pairwise")
     ap.add_argument("--fp64-steps", type=int, default=20_000,
@@ -183,7 +186,8 @@ def run_ours(args, rank, world, device):
     if args.workload in ("sweep", "plain", "fig2"):
         w = {"sweep": lambda r: sweep_workload(r, args), "plain": plain_workload,
              "fig2": fig2_workload}[args.workload](rank)
-        sched = sde.SDE_SCHED_PLAIN if args.workload == "plain" else sde.SDE_SCHED_PERSISTENT
+        plain = args.schedule == "plain" or (args.schedule == "auto" and args.workload == "plain")
+        sched = sde.SDE_SCHED_PLAIN if plain else sde.SDE_SCHED_PERSISTENT
         ens = sde.Ensemble.josephson(w["points"], w["paths"], w["steps"], w["seed"],
                                      steps_per_period=w["steps_per_period"], schedule=sched,
                                      block_threads=args.block, paths_per_thread=args.ilp,
@@ -220,6 +224,8 @@ def run_ours(args, rank, world, device):
             name += "_cap%d" % args.steps_cap
         if args.euler:
             name += "_euler"
+        if args.workload != "plain" and sched == sde.SDE_SCHED_PLAIN:
+            name += "_plain_per_point"
         cfg = {"workload": name,
                "points": len(w["points"]), "total_paths": n, "path_steps": units,
                "steps_per_period": w["steps_per_period"],
