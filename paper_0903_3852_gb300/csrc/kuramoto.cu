@@ -732,12 +732,15 @@ struct MfShape {
 };
 
 // Candidate shapes for the mean-field kernel: one CTA per replica, or a
-// cluster of 2 or 4 CTAs per replica (distributed shared memory reductions).
+// cluster of 2, 4 or 8 CTAs per replica (distributed shared memory
+// reductions; more, smaller CTAs let co-resident replicas overlap each
+// other's barrier latency).
 std::vector<MfShape> meanfield_candidates(int64_t N) {
   std::vector<MfShape> out;
-  for (int cs : {1, 2, 4}) {
+  for (int cs : {1, 2, 4, 8}) {
     const int64_t chunk = (N + cs - 1) / cs;
-    for (int block : {256, 512, 1024}) {
+    for (int block : {128, 256, 512, 1024}) {
+      if (block == 128 && cs < 8) continue;
       if (cs > 1 && cs * (block / 32) > 32) continue;  // one exchange slot per warp of the cluster
       if (block > ((chunk + 31) / 32) * 32 && block > 256) continue;  // mostly idle threads
       const int opt = pow2_at_least((chunk + block - 1) / block);
@@ -966,8 +969,8 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   }
   // Launch shape.
   SDE_CHECK_ARG(cfg->cluster_ctas == 0 || cfg->cluster_ctas == 1 || cfg->cluster_ctas == 2 ||
-                    cfg->cluster_ctas == 4,
-                "cluster_ctas must be 0, 1, 2 or 4");
+                    cfg->cluster_ctas == 4 || cfg->cluster_ctas == 8,
+                "cluster_ctas must be 0, 1, 2, 4 or 8");
   if (grid_forced) {
     k->cs = 0;
     k->block = kMfgThreads;
@@ -977,6 +980,20 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
       kuramoto_destroy(k);
       return st;
     }
+  } else if (cfg->model == SDE_KURAMOTO_MEANFIELD && cfg->cluster_ctas > 1) {
+    // a fixed cluster shape: cs CTAs of block threads per replica
+    const int cs = cfg->cluster_ctas, block = cfg->block_threads;
+    const int64_t chunk = (k->N + cs - 1) / cs;
+    const int opt = pow2_at_least((chunk + block - 1) / block);
+    if (block < 32 || block % 32 != 0 || block > 512 || cs * (block / 32) > 32 || opt > 8) {
+      kuramoto_destroy(k);
+      set_error("invalid argument: with cluster_ctas > 1, block_threads must be a multiple of 32, at most "
+                "512 and at most 32 warps per cluster, with at most 8 oscillators per thread");
+      return SDE_ERR_INVALID_ARG;
+    }
+    k->cs = cs;
+    k->block = block;
+    k->opt = opt;
   } else if (cfg->model == SDE_KURAMOTO_MEANFIELD) {
     int block = cfg->block_threads;
     int opt = pow2_at_least((k->N + block - 1) / block);

@@ -45,7 +45,9 @@ def _sensitivity(phi0, omega, D, dt, steps, seed, r, Kconst, meanfield, trials=3
 
 
 @pytest.mark.parametrize("N,R,block,cluster", [(1000, 3, 0, 0), (4096, 2, 0, 0), (4096, 2, 256, 0), (37, 2, 0, 0),
-                                               (4096, 3, 0, 2), (1000, 2, 0, 4), (37, 2, 0, 4)])
+                                               (4096, 3, 0, 2), (1000, 2, 0, 4), (37, 2, 0, 4),
+                                               (4096, 2, 0, 8), (1000, 3, 0, 8), (4096, 2, 128, 8),
+                                               (1000, 2, 256, 4)])
 def test_meanfield_pathwise(N, R, block, cluster):
     steps, M, seed = 1000, 100, 7
     w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=3)
