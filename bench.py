@@ -473,6 +473,9 @@ def run_ours(args, rank, world, device):
     elif args.workload == "kuramoto-general" and not args.fused:
         traffic = 146.2e6  # tc_gemm_bf16_kernel: K (134 MB) once + operands and output
         traffic_src = "profiles/tc_gemm_bf16_kernel_N8192_R256.md"
+    elif args.workload == "kuramoto-meanfield":
+        traffic = 2.16e6  # phases and omega read once per run; results stay in L2
+        traffic_src = "profiles/kur_meanfield_cluster_kernel_N4096_R64.md"
     elif args.workload == "kuramoto-pairwise" and not args.euler:
         traffic = 2.12e6
         traffic_src = "profiles/kur_pairwise_stage_N4096_R64.md"
