@@ -53,6 +53,8 @@ def parse():
                     help="kuramoto-fig4: steps per bench step (default: the workload's 2000)")
     ap.add_argument("--cluster", type=int, default=0,
                     help="kuramoto-meanfield: CTAs per replica (with --block: skips autotuning)")
+    ap.add_argument("--async-exchange", action="store_true",
+                    help="kuramoto-meanfield: cluster exchange by st.async + mbarrier only")
     ap.add_argument("--schedule", choices=["auto", "plain", "persistent"], default="auto",
                     help="Josephson workloads: persistent sweep launch (default except 'plain') or one "
                          "launch per point with one thread per path (the plain per-path kernel)")
@@ -299,7 +301,8 @@ def run_ours(args, rank, world, device):
             dict(block_threads=args.block, cluster_ctas=args.cluster)
         ens = sde.Ensemble.kuramoto(model, w["n_osc"], w["replicas"], w["K"], w["D"], w["dt"], w["seed"],
                                     sample_every=w["sample_every"],
-                                    flags=sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_EULER if euler else 0),
+                                    flags=sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_EULER if euler else 0)
+                                    | (sde.SDE_FLAG_ASYNC_EXCHANGE if args.async_exchange else 0),
                                     **mf_shape)
         phi_h = torch.from_numpy(w["phi0"]).pin_memory()
         phi_in = phi_h.to(device)

@@ -76,6 +76,10 @@ typedef enum sde_schedule {
 #define SDE_FLAG_FUSED 4u        /* general coupling, tensor-core form: run the SRK2
                                     sub-steps in the GEMM epilogue instead of as
                                     separate kernels (same results bit for bit) */
+#define SDE_FLAG_ASYNC_EXCHANGE 16u /* Kuramoto mean field in clusters: exchange the partial sums
+                                        by asynchronous remote stores that complete on the
+                                        receiving CTA's mbarrier, instead of a cluster barrier
+                                        (the autotuner tries both forms when unset) */
 #define SDE_FLAG_EULER 8u        /* Euler-Maruyama instead of SRK2 (Alg. 2): the
                                     first-order scheme of PROG2 (Sec. 4.2).
                                     Josephson: every schedule, same kernels with

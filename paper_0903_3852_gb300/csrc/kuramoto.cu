@@ -290,6 +290,201 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
   cluster.sync();  // no CTA leaves while others may still read its exchange slots
 }
 
+// ---- cluster exchange by asynchronous remote stores ----------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait (at most ~1 s) for the phase `parity` of an mbarrier; false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (now_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// The cluster mean field with the exchange done by st.async: every warp
+// sends its (S, C) pair into its slot of every CTA of the cluster with an
+// asynchronous remote store that completes on the receiving CTA's mbarrier
+// (transaction bytes), and each CTA waits on its own mbarrier for the
+// cs x warps pairs of the stage instead of a cluster-wide barrier (whose
+// release/acquire fence is what the plain cluster kernel waits on).  Two
+// slot buffers and two mbarriers alternate by stage: a CTA can only send
+// stage s + 2 after receiving everyone's stage s + 1 pairs, each sent after
+// its sender had read the stage s slots, so a buffer is never overwritten
+// while it is read, and the receiver has re-armed the buffer's mbarrier
+// (after its own stage s wait, before its stage s + 1 sends) before any
+// stage s + 2 store can arrive.  Waits are bounded (~1 s): on expiry the kernel records
+// kErrTimeout, leaves the step loop (warp-uniformly) and meets the others at
+// the final cluster barrier.
+template <int OPT>
+__global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurArgs A) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ float2 slots[2][32];
+  __shared__ __align__(8) uint64_t mbar[2];
+  const int cs = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nslots = cs * nwarps;  // <= 32, checked by the host
+  const uint32_t bytes = (uint32_t)nslots * 8u;
+  if (threadIdx.x == 0) {
+    // each phase is armed (arrival + expected bytes) before any store of it can
+    // arrive: stages 0 and 1 here, stage s + 2 right after stage s completes
+    // (no sender reaches stage s + 2 before this CTA has sent stage s + 1)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(bytes)
+                 : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(bytes)
+                 : "memory");
+  }
+  cluster.sync();  // every CTA's barriers exist and are armed before the first remote store
+  const int rep = blockIdx.x / cs;
+  const int64_t N = A.N;
+  const int64_t chunk = (N + cs - 1) / cs;
+  const int64_t i0 = (int64_t)crank * chunk;
+  const int64_t base = (int64_t)rep * N;
+  const uint2 key = seed_to_key(A.seed);
+  uint32_t th[OPT];
+  float wdt[OPT];
+  bool valid[OPT];
+  uint32_t oid[OPT];
+#pragma unroll
+  for (int k = 0; k < OPT; ++k) {
+    const int64_t li = threadIdx.x + (int64_t)k * blockDim.x;
+    const int64_t i = i0 + li;
+    valid[k] = li < chunk && i < N;
+    oid[k] = (uint32_t)i;
+    th[k] = valid[k] ? A.theta_in[base + i] : 0u;
+    wdt[k] = valid[k] ? A.omega[base + i] * A.wscale : 0.0f;
+  }
+  // remote addresses of this warp's slot and of the mbarriers, in CTA `lane`
+  const uint32_t my_slot0 = smem_u32(&slots[0][crank * nwarps + warp]);
+  const uint32_t my_slot1 = smem_u32(&slots[1][crank * nwarps + warp]);
+  const uint32_t rslot0 = lane < cs ? cluster_map(my_slot0, (uint32_t)lane) : 0u;
+  const uint32_t rslot1 = lane < cs ? cluster_map(my_slot1, (uint32_t)lane) : 0u;
+  const uint32_t rbar0 = lane < cs ? cluster_map(smem_u32(&mbar[0]), (uint32_t)lane) : 0u;
+  const uint32_t rbar1 = lane < cs ? cluster_map(smem_u32(&mbar[1]), (uint32_t)lane) : 0u;
+  uint32_t stage = 0;
+  bool failed = false;  // warp-uniform
+  auto cluster_sum = [&](float S, float C) -> float2 {
+    const float2 part = warp_sum2(S, C);
+    const int b = (int)(stage & 1u);
+    const uint32_t parity = (stage >> 1) & 1u;
+    const uint32_t bar = smem_u32(&mbar[b]);
+    if (lane < cs)
+      asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+                       b ? rslot1 : rslot0),
+                   "f"(part.x), "f"(part.y), "r"(b ? rbar1 : rbar0)
+                   : "memory");
+    const bool ok = mbar_wait_bounded(bar, parity);
+    if (__any_sync(0xffffffffu, !ok)) {
+      failed = true;
+      if (lane == 0) atomicOr(A.err, kErrTimeout);
+    }
+    if (threadIdx.x == 0 && ok)  // arm this buffer's next phase (stage + 2)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    const float2 v = lane < nslots ? slots[b][lane] : make_float2(0.0f, 0.0f);
+    ++stage;
+    return warp_sum2(v.x, v.y);
+  };
+  int64_t sample_ctr = 0, sample_idx = 0;
+  for (int64_t n = A.n_begin; n < A.n_end && !failed;) {
+    const int64_t g = n >> 2;
+    float z[OPT][4];
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) gauss4((uint32_t)g, oid[k], (uint32_t)rep, kTagKuramoto, key, z[k]);
+    const int s0 = (int)(n & 3);
+    const int64_t rem = A.n_end - (g << 2);
+    const int s1 = rem < 4 ? (int)rem : 4;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (s < s0 || s >= s1 || failed) continue;
+      float sn[OPT], cs_[OPT];
+      float S = 0.0f, C = 0.0f;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        sincos_turns(th[k], sn[k], cs_[k]);
+        if (!valid[k]) sn[k] = cs_[k] = 0.0f;
+        S += sn[k];
+        C += cs_[k];
+      }
+      float2 sc = cluster_sum(S, C);
+      if (A.M > 0 && sample_ctr == 0) {
+        if (threadIdx.x == 0 && crank == 0 && A.r_out) {
+          const double Sd = sc.x, Cd = sc.y;
+          A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+        }
+        ++sample_idx;
+      }
+      if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
+      float g1[OPT], sn2[OPT], cs2[OPT];
+      float S2 = 0.0f, C2 = 0.0f;
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
+        const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
+        sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
+        if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
+        S2 += sn2[k];
+        C2 += cs2[k];
+      }
+      sc = cluster_sum(S2, C2);
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
+        const float g2 = cs2[k] * sc.x - sn2[k] * sc.y;
+        const float d = fmaf(A.sc, z[k][s], fmaf(A.kh, g1[k] + g2, wdt[k]));
+        th[k] += (uint32_t)__float2int_rn(d * 4294967296.0f);
+      }
+    }
+    n = (g + 1) << 2;
+  }
+  if (A.M > 0 && !failed) {
+    float S = 0.0f, C = 0.0f;
+#pragma unroll
+    for (int k = 0; k < OPT; ++k) {
+      float sn, c;
+      sincos_turns(th[k], sn, c);
+      if (valid[k]) {
+        S += sn;
+        C += c;
+      }
+    }
+    const float2 sc = cluster_sum(S, C);
+    if (threadIdx.x == 0 && crank == 0 && A.r_out) {
+      const double Sd = sc.x, Cd = sc.y;
+      A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < OPT; ++k)
+    if (valid[k]) A.theta_out[base + oid[k]] = th[k];
+  cluster.sync();  // no CTA leaves while remote stores into it may be in flight
+}
+
 // ---- mean field over the whole grid ------------------------------------
 
 constexpr int kMfgThreads = 256;
@@ -647,7 +842,7 @@ void *mf_kernel_ptr() {
 }
 
 template <int OPT>
-cudaError_t launch_mf_cluster(const KurArgs &a, int block, int cs, cudaStream_t s) {
+cudaError_t launch_mf_cluster(const KurArgs &a, int block, int cs, bool async, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.R * cs));
   cfg.blockDim = dim3((unsigned)block);
@@ -660,18 +855,19 @@ cudaError_t launch_mf_cluster(const KurArgs &a, int block, int cs, cudaStream_t 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (async) return cudaLaunchKernelEx(&cfg, kur_meanfield_async_kernel<OPT>, a);
   return cudaLaunchKernelEx(&cfg, kur_meanfield_cluster_kernel<OPT>, a);
 }
 
 // cs > 1: one replica per cluster of cs CTAs (opt oscillators per thread of
 // each CTA); cs == 1: one CTA per replica.
-cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, int cs, cudaStream_t s) {
+cudaError_t launch_meanfield(const KurArgs &a, int block, int opt, int cs, bool async, cudaStream_t s) {
   if (cs > 1) {
     switch (opt) {
-      case 1: return launch_mf_cluster<1>(a, block, cs, s);
-      case 2: return launch_mf_cluster<2>(a, block, cs, s);
-      case 4: return launch_mf_cluster<4>(a, block, cs, s);
-      case 8: return launch_mf_cluster<8>(a, block, cs, s);
+      case 1: return launch_mf_cluster<1>(a, block, cs, async, s);
+      case 2: return launch_mf_cluster<2>(a, block, cs, async, s);
+      case 4: return launch_mf_cluster<4>(a, block, cs, async, s);
+      case 8: return launch_mf_cluster<8>(a, block, cs, async, s);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -729,6 +925,7 @@ namespace {
 
 struct MfShape {
   int cs, block, opt;
+  bool async;  // cluster exchange by st.async + mbarrier instead of a cluster barrier
 };
 
 // Candidate shapes for the mean-field kernel: one CTA per replica, or a
@@ -747,7 +944,8 @@ std::vector<MfShape> meanfield_candidates(int64_t N) {
       const int max_opt = cs > 1 ? 8 : 16;
       const int max_block = cs > 1 ? 512 : (opt <= 2 ? 1024 : 512);
       if (opt > max_opt || block > max_block) continue;
-      out.push_back({cs, block, opt});
+      out.push_back({cs, block, opt, false});
+      if (cs > 1) out.push_back({cs, block, opt, true});
     }
   }
   return out;
@@ -812,7 +1010,14 @@ sde_status run_meanfield_grid(KuramotoCtx *k, int64_t n_begin, int64_t n_end, co
 // fastest.
 sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
   auto cands = meanfield_candidates(k->N);
-  if (with_grid && only_cs == 0) cands.push_back({0, kMfgThreads, 0});
+  if (k->flags & SDE_FLAG_ASYNC_EXCHANGE) {
+    std::vector<MfShape> keep;
+    for (const auto &c : cands)
+      if (c.async) keep.push_back(c);
+    cands.swap(keep);
+  } else if (with_grid && only_cs == 0) {
+    cands.push_back({0, kMfgThreads, 0, false});
+  }
   if (only_cs > 0) {
     std::vector<MfShape> keep;
     for (const auto &c : cands)
@@ -863,7 +1068,7 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
           st = run_meanfield_grid(k, a.n_begin, a.n_end, omega, nullptr, 0, s);
           k->flags = flags;
           if (st != SDE_OK) break;
-        } else if ((e = launch_meanfield(a, c.block, c.opt, c.cs, s)) != cudaSuccess) {
+        } else if ((e = launch_meanfield(a, c.block, c.opt, c.cs, c.async, s)) != cudaSuccess) {
           st = cuda_fail(e, "mean-field autotune launch");
           break;
         }
@@ -880,6 +1085,7 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
       if (tmin < best) {
         best = tmin;
         k->cs = c.cs;
+        k->mf_async = c.async;
         k->block = c.block;
         k->opt = c.opt;
       }
@@ -889,6 +1095,7 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
   if (e1) cudaEventDestroy(e1);
   if (s) cudaStreamDestroy(s);
   cudaFree(omega);
+  if (st == SDE_OK) cudaMemset(k->err, 0, sizeof(uint32_t));  // scratch runs report nothing
   return st;
 }
 
@@ -994,6 +1201,7 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
     k->cs = cs;
     k->block = block;
     k->opt = opt;
+    k->mf_async = (cfg->flags & SDE_FLAG_ASYNC_EXCHANGE) != 0;
   } else if (cfg->model == SDE_KURAMOTO_MEANFIELD) {
     int block = cfg->block_threads;
     int opt = pow2_at_least((k->N + block - 1) / block);
@@ -1124,7 +1332,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
     a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
     a.seed = k->seed;
     a.err = k->err;
-    SDE_CUDA_TRY(launch_meanfield(a, k->block, k->opt, k->cs, s));
+    SDE_CUDA_TRY(launch_meanfield(a, k->block, k->opt, k->cs, k->mf_async, s));
   } else if (k->model == SDE_KURAMOTO_PAIRWISE) {
     KurPairArgs a{};
     a.theta = k->theta;

@@ -23,6 +23,7 @@ struct KuramotoCtx {
   uint32_t flags = 0;
   int block = 0, opt = 0;
   int cs = 1;  // mean field: CTAs per replica (thread-block cluster size); 0 = grid-wide form
+  bool mf_async = false;  // cluster exchange by asynchronous remote stores + mbarrier
   // grid-wide mean field: per-replica partial sums, totals and block counters
   int mfg_blocks = 0;             // blocks per replica, the largest of mfg_grid
   int mfg_grid[4] = {0, 0, 0, 0}; // blocks per replica: predictor, corrector, sums, predictor drawing noise

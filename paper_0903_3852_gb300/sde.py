@@ -32,6 +32,7 @@ SDE_FLAG_NO_GRAPH = 1
 SDE_FLAG_TIME_KERNELS = 2
 SDE_FLAG_FUSED = 4
 SDE_FLAG_EULER = 8
+SDE_FLAG_ASYNC_EXCHANGE = 16
 
 
 class SDEError(RuntimeError):

@@ -44,15 +44,20 @@ def _sensitivity(phi0, omega, D, dt, steps, seed, r, Kconst, meanfield, trials=3
     return G
 
 
-@pytest.mark.parametrize("N,R,block,cluster", [(1000, 3, 0, 0), (4096, 2, 0, 0), (4096, 2, 256, 0), (37, 2, 0, 0),
-                                               (4096, 3, 0, 2), (1000, 2, 0, 4), (37, 2, 0, 4),
-                                               (4096, 2, 0, 8), (1000, 3, 0, 8), (4096, 2, 128, 8),
-                                               (1000, 2, 256, 4)])
-def test_meanfield_pathwise(N, R, block, cluster):
+AX = sde.SDE_FLAG_ASYNC_EXCHANGE
+
+
+@pytest.mark.parametrize("N,R,block,cluster,flags", [
+    (1000, 3, 0, 0, 0), (4096, 2, 0, 0, 0), (4096, 2, 256, 0, 0), (37, 2, 0, 0, 0),
+    (4096, 3, 0, 2, 0), (1000, 2, 0, 4, 0), (37, 2, 0, 4, 0), (4096, 2, 0, 8, 0), (1000, 3, 0, 8, 0),
+    (4096, 2, 128, 8, 0), (1000, 2, 256, 4, 0),
+    # partial sums exchanged by asynchronous remote stores completing on mbarriers
+    (4096, 3, 0, 2, AX), (1000, 2, 256, 4, AX), (37, 2, 128, 8, AX), (4096, 2, 512, 2, AX)])
+def test_meanfield_pathwise(N, R, block, cluster, flags):
     steps, M, seed = 1000, 100, 7
     w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=3)
     ens = _ens(sde.SDE_KURAMOTO_MEANFIELD, N, R, 2.0, 0.05, 0.01, seed, M, block_threads=block,
-               cluster_ctas=cluster)
+               cluster_ctas=cluster, flags=flags)
     if cluster:
         assert ens.tuning()[2] == cluster
     phig, rg, obs = kur_run(ens, w["phi0"], w["omega"], 0, steps)
