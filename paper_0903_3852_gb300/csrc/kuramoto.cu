@@ -540,29 +540,37 @@ __global__ void __launch_bounds__(kMfgThreads, MODE == 3 ? 4 : (MODE == 2 ? 8 : 
   }
   const int j = (int)(A.n & 3);
   float ps = 0.0f, pc = 0.0f;
-  const int64_t stride = (int64_t)gridDim.x * kMfgThreads * kMfgIlp;
-  for (int64_t i0 = (int64_t)blockIdx.x * kMfgThreads * kMfgIlp + threadIdx.x; i0 < N; i0 += stride) {
+  // per-replica base pointers, 32-bit oscillator indices (N < 2^31, so
+  // i0 + stride < 2^32 never wraps)
+  const uint32_t Nu = (uint32_t)N;
+  uint32_t *th_r = A.theta + base;
+  uint32_t *tt_r = A.theta_t + base;
+  float *y_r = A.y + base;
+  const float *om_r = A.omega + base;
+  const float *psi_in = (kPred && !kGen && j > 0) ? A.psi + (int64_t)(j - 1) * NR + base : nullptr;
+  float *psi_out = A.psi + base;  // plane k - 1 at + (k - 1) NR
+  const uint32_t stride = gridDim.x * (uint32_t)(kMfgThreads * kMfgIlp);
+  for (uint32_t i0 = blockIdx.x * (uint32_t)(kMfgThreads * kMfgIlp) + threadIdx.x; i0 < Nu; i0 += stride) {
     uint32_t t0[kMfgIlp], tt[kMfgIlp];
     float a1[kMfgIlp], a2[kMfgIlp];
     bool ok[kMfgIlp];
 #pragma unroll
     for (int u = 0; u < kMfgIlp; ++u) {
-      const int64_t i = i0 + u * kMfgThreads;
-      ok[u] = i < N;
-      const int64_t gi = base + (ok[u] ? i : 0);
-      t0[u] = A.theta[gi];
+      const uint32_t i = i0 + u * kMfgThreads;
+      ok[u] = i < Nu;
+      const uint32_t ii = ok[u] ? i : 0u;
+      t0[u] = th_r[ii];
       if (kPred) {
-        a1[u] = A.omega[gi];
-        a2[u] = kGen ? 0.0f : A.psi[(int64_t)(j - 1) * NR + gi];
+        a1[u] = om_r[ii];
+        a2[u] = kGen ? 0.0f : psi_in[ii];
       } else if (MODE == 1) {
-        tt[u] = A.theta_t[gi];
-        a1[u] = A.y[gi];
+        tt[u] = tt_r[ii];
+        a1[u] = y_r[ii];
       }
     }
 #pragma unroll
     for (int u = 0; u < kMfgIlp; ++u) {
-      const int64_t i = i0 + u * kMfgThreads;
-      const int64_t gi = base + i;
+      const uint32_t i = i0 + u * kMfgThreads;
       float sn, cs;
       if (MODE == 2) {
         sincos_turns(t0[u], sn, cs);
@@ -573,20 +581,20 @@ __global__ void __launch_bounds__(kMfgThreads, MODE == 3 ? 4 : (MODE == 2 ? 8 : 
         float psi = a2[u];
         if (kGen) {
           float z[4];
-          gauss4((uint32_t)(A.n >> 2), (uint32_t)i, (uint32_t)rep, kTagKuramoto, A.keys, z);
+          gauss4((uint32_t)(A.n >> 2), i, (uint32_t)rep, kTagKuramoto, A.keys, z);
           psi = pick4(z, j);
           if (ok[u]) {
 #pragma unroll
             for (int k = 1; k < 4; ++k)
-              if (k > j) A.psi[(int64_t)(k - 1) * NR + gi] = z[k];
+              if (k > j) psi_out[(int64_t)(k - 1) * NR + i] = z[k];
           }
         }
         const float wdt = a1[u] * A.wscale;
         const float d1 = fmaf(A.sc, psi, fmaf(A.kc, g1, wdt));
         const uint32_t tp = t0[u] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
         if (ok[u]) {
-          A.theta_t[gi] = tp;
-          A.y[gi] = fmaf(A.sc, psi, fmaf(A.kh, g1, wdt));
+          tt_r[i] = tp;
+          y_r[i] = fmaf(A.sc, psi, fmaf(A.kh, g1, wdt));
         }
         sincos_turns(tp, sn, cs);
       } else {
@@ -594,7 +602,7 @@ __global__ void __launch_bounds__(kMfgThreads, MODE == 3 ? 4 : (MODE == 2 ? 8 : 
         sincos_turns(tt[u], s2, c2);
         const float g2 = c2 * S - s2 * C;
         const uint32_t t1 = t0[u] + (uint32_t)__float2int_rn(fmaf(A.kh, g2, a1[u]) * 4294967296.0f);
-        if (ok[u]) A.theta[gi] = t1;
+        if (ok[u]) th_r[i] = t1;
         sincos_turns(t1, sn, cs);
       }
       if (ok[u]) {
