@@ -825,7 +825,7 @@ def main():
         return
     res, ens = run_ours(args, rank, world, local)
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # the oracle baseline is a 1-GPU figure
             res["cpu_baseline"] = cpu_baseline_both(args)
         print(json.dumps(res))
     ens.close()
