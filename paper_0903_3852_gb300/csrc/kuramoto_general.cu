@@ -32,10 +32,6 @@ namespace sde {
 
 namespace {
 
-constexpr float kTurn = 2.3283064365386963e-10f;  // 2^-32
-
-__device__ __forceinline__ float signed_turns(uint32_t th) { return (float)(int32_t)th * kTurn; }
-
 template <typename T>
 __device__ __forceinline__ T to_op(float v);
 template <>
@@ -54,7 +50,7 @@ __global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   float s, c;
-  sincospif(2.0f * signed_turns(theta[r * N + i]), &s, &c);
+  sincos_turns(theta[r * N + i], s, c);
   op[(2 * r) * N + i] = to_op<T>(s);
   op[(2 * r + 1) * N + i] = to_op<T>(c);
 }
@@ -63,13 +59,43 @@ __global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N) {
 // (the forms without the fused epilogue): the same per-element update as the
 // tensor-core epilogue (tc::stage_element), the next operand written as T.
 // Grid: (N / 256, R).
+// kStageIlp elements per thread (i, i + 256, ...): every input of the group is
+// loaded before any arithmetic, so each thread keeps several loads in flight.
+constexpr int kStageIlp = 4;
+
 template <int STAGE, typename T>
-__global__ void kg_stage_kernel(const float *__restrict__ Dt, const tc::StageArgs a, T *op_next) {
+__global__ void __launch_bounds__(256) kg_stage_kernel(const float *__restrict__ Dt, const tc::StageArgs a,
+                                                       T *op_next) {
   const int64_t r = blockIdx.y;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
-  tc::stage_element<STAGE>(a, op_next, r, i, Dt[(2 * r) * a.N + i], Dt[(2 * r + 1) * a.N + i],
-                           seed_to_key(a.seed));
+  const int64_t N = a.N;
+  const int64_t i0 = (int64_t)blockIdx.x * (256 * kStageIlp) + threadIdx.x;
+  const uint2 key = seed_to_key(a.seed);
+  uint32_t th[kStageIlp], th_s[kStageIlp];
+  float ps[kStageIlp], pc[kStageIlp], om[kStageIlp], psi[kStageIlp], g1[kStageIlp];
+  bool ok[kStageIlp];
+#pragma unroll
+  for (int u = 0; u < kStageIlp; ++u) {
+    const int64_t i = i0 + u * 256;
+    ok[u] = i < N;
+    const int64_t ii = ok[u] ? i : 0;
+    const int64_t idx = r * N + ii;
+    ps[u] = Dt[(2 * r) * N + ii];
+    pc[u] = Dt[(2 * r + 1) * N + ii];
+    th[u] = a.theta[idx];
+    th_s[u] = STAGE == 0 ? th[u] : a.theta_t[idx];
+    om[u] = a.omega[idx];
+    g1[u] = STAGE == 1 ? a.g1[idx] : 0.0f;
+    psi[u] = (STAGE == 0 && a.fresh) ? 0.0f : a.psi4[(a.n & 3) * a.NR + idx];
+  }
+#pragma unroll
+  for (int u = 0; u < kStageIlp; ++u) {
+    if (!ok[u]) continue;
+    const int64_t i = i0 + u * 256;
+    const int64_t idx = r * N + i;
+    if (STAGE == 0 && a.fresh) psi[u] = tc::stage_noise<STAGE>(a, r, i, idx, key);
+    const tc::StageOut o = tc::stage_math<STAGE>(a, th_s[u], th[u], om[u], psi[u], g1[u], ps[u], pc[u]);
+    tc::stage_store<STAGE>(a, op_next, r, i, idx, o);
+  }
 }
 
 // Coupling sums alone: out[r][i] = cos x_i Dt[2r][i] - sin x_i Dt[2r+1][i].
@@ -78,7 +104,7 @@ __global__ void kg_coupling_kernel(const float *__restrict__ Dt, const uint32_t 
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   float s, c;
-  sincospif(2.0f * signed_turns(theta[r * N + i]), &s, &c);
+  sincos_turns(theta[r * N + i], s, c);
   out[r * N + i] = c * Dt[(2 * r) * N + i] - s * Dt[(2 * r + 1) * N + i];
 }
 
@@ -275,6 +301,9 @@ cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s, int epi = tc:
 }
 
 dim3 grid_nr(const KuramotoCtx *k) { return dim3((unsigned)((k->N + 255) / 256), (unsigned)k->R); }
+dim3 grid_stage(const KuramotoCtx *k) {
+  return dim3((unsigned)((k->N + 256 * kStageIlp - 1) / (256 * kStageIlp)), (unsigned)k->R);
+}
 
 cudaError_t launch_operand(KuramotoCtx *k, int which, cudaStream_t s) {
   if (is_tc(k))
@@ -290,9 +319,9 @@ cudaError_t launch_stage(KuramotoCtx *k, int next, const float *omega, int64_t n
                          cudaStream_t s) {
   const tc::StageArgs a = stage_args(k, next, omega, n, run_begin);
   if (is_tc(k))
-    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid_nr(k), 256, 0, s>>>(k->P, a, (__nv_bfloat16 *)op_buf(k, next));
+    kg_stage_kernel<STAGE, __nv_bfloat16><<<grid_stage(k), 256, 0, s>>>(k->P, a, (__nv_bfloat16 *)op_buf(k, next));
   else
-    kg_stage_kernel<STAGE, float><<<grid_nr(k), 256, 0, s>>>(k->P, a, (float *)op_buf(k, next));
+    kg_stage_kernel<STAGE, float><<<grid_stage(k), 256, 0, s>>>(k->P, a, (float *)op_buf(k, next));
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@
 
 #include "common.cuh"
 #include "philox.cuh"
+#include "turns.cuh"
 
 namespace sde {
 namespace tc {
@@ -178,7 +179,6 @@ struct StageArgs {
 
 enum { EPI_STORE_D = 0, EPI_STAGE0 = 1, EPI_STAGE1 = 2 };
 
-__device__ __forceinline__ float signed_turns_tc(uint32_t th) { return (float)(int32_t)th * 2.3283064365386963e-10f; }
 
 // One element of a stage: oscillator i of replica r with coupling
 // components ps = (K sin x)_i, pc = (K cos x)_i.  The Gaussians of a 4-step
@@ -190,41 +190,75 @@ __device__ __forceinline__ void store_operand(__nv_bfloat16 *op, int64_t idx, fl
 }
 __device__ __forceinline__ void store_operand(float *op, int64_t idx, float v) { op[idx] = v; }
 
-template <int STAGE, typename T>
-__device__ __forceinline__ void stage_element(const StageArgs &a, T *op_next, int64_t r, int64_t i, float ps,
-                                              float pc, uint2 key) {
-  const int64_t idx = r * a.N + i;
-  const uint32_t th_i = STAGE == 0 ? a.theta[idx] : a.theta_t[idx];
+// The SRK2 sub-step of one element (replica r, oscillator i) from its loaded
+// inputs: th_s the phase the coupling is taken at (theta for the predictor,
+// theta~ for the corrector), th the current theta, the GEMM outputs (ps, pc),
+// omega_i, the Gaussian psi and (corrector) the first-stage sum g1.  Shared
+// by the separate stage kernel and the fused GEMM epilogue, so both compute
+// bit for bit the same values.
+struct StageOut {
+  uint32_t out;  // theta~ (predictor) or the new theta (corrector)
+  float g;       // this stage's coupling sum
+  float so, co;  // sin, cos of `out`: the next GEMM operand
+};
+
+template <int STAGE>
+__device__ __forceinline__ StageOut stage_math(const StageArgs &a, uint32_t th_s, uint32_t th, float omega,
+                                               float psi, float g1, float ps, float pc) {
+  StageOut o;
   float s, c;
-  sincospif(2.0f * signed_turns_tc(th_i), &s, &c);
-  const float g = c * ps - s * pc;
-  const float wdt = a.omega[idx] * a.wscale;
+  sincos_turns(th_s, s, c);
+  o.g = c * ps - s * pc;
+  const float wdt = omega * a.wscale;
+  if (STAGE == 0) {
+    const float d1 = fmaf(a.sc, psi, fmaf(a.kc, o.g, wdt));
+    o.out = th + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+  } else {
+    const float d = fmaf(a.sc, psi, fmaf(a.kh, g1 + o.g, wdt));
+    o.out = th + (uint32_t)__float2int_rn(d * 4294967296.0f);
+  }
+  sincos_turns(o.out, o.so, o.co);
+  return o;
+}
+
+// The Gaussian of step n for element idx: drawn from the Philox block at the
+// predictor of the block's first step (or of a run), which also keeps the
+// block's later elements in psi4; read from psi4 otherwise.
+template <int STAGE>
+__device__ __forceinline__ float stage_noise(const StageArgs &a, int64_t r, int64_t i, int64_t idx, uint2 key) {
   const int q = (int)(a.n & 3);
-  float psi;
   if (STAGE == 0 && a.fresh) {
     float zz[4];
     gauss4((uint32_t)(a.n >> 2), (uint32_t)i, (uint32_t)r, kTagKuramoto, key, zz);
     for (int k = q; k < 4; ++k) a.psi4[k * a.NR + idx] = zz[k];
-    psi = pick4(zz, q);
-  } else {
-    psi = a.psi4[q * a.NR + idx];
+    return pick4(zz, q);
   }
+  return a.psi4[q * a.NR + idx];
+}
 
-  uint32_t out;
+template <int STAGE, typename T>
+__device__ __forceinline__ void stage_store(const StageArgs &a, T *op_next, int64_t r, int64_t i, int64_t idx,
+                                            const StageOut &o) {
   if (STAGE == 0) {
-    const float d1 = fmaf(a.sc, psi, fmaf(a.kc, g, wdt));
-    out = a.theta[idx] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
-    a.theta_t[idx] = out;
-    a.g1[idx] = g;
+    a.theta_t[idx] = o.out;
+    a.g1[idx] = o.g;
   } else {
-    const float d = fmaf(a.sc, psi, fmaf(a.kh, a.g1[idx] + g, wdt));
-    out = a.theta[idx] + (uint32_t)__float2int_rn(d * 4294967296.0f);
-    a.theta[idx] = out;
+    a.theta[idx] = o.out;
   }
-  float so, co;
-  sincospif(2.0f * signed_turns_tc(out), &so, &co);
-  store_operand(op_next, (2 * r) * a.N + i, so);
-  store_operand(op_next, (2 * r + 1) * a.N + i, co);
+  store_operand(op_next, (2 * r) * a.N + i, o.so);
+  store_operand(op_next, (2 * r + 1) * a.N + i, o.co);
+}
+
+template <int STAGE, typename T>
+__device__ __forceinline__ void stage_element(const StageArgs &a, T *op_next, int64_t r, int64_t i, float ps,
+                                              float pc, uint2 key) {
+  const int64_t idx = r * a.N + i;
+  const uint32_t th = a.theta[idx];
+  const uint32_t th_s = STAGE == 0 ? th : a.theta_t[idx];
+  const float psi = stage_noise<STAGE>(a, r, i, idx, key);
+  const float g1 = STAGE == 1 ? a.g1[idx] : 0.0f;
+  const StageOut o = stage_math<STAGE>(a, th_s, th, a.omega[idx], psi, g1, ps, pc);
+  stage_store<STAGE>(a, op_next, r, i, idx, o);
 }
 
 // D = A * B^T over K = Kdim.  EPI_STORE_D writes Dt transposed ([col][row],
