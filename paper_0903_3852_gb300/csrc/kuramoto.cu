@@ -64,11 +64,41 @@ __device__ __forceinline__ float2 block_sum2(float a, float b, float2 *red) {
   return warp_sum2(v.x, v.y);
 }
 
+// Partial sums of sin and cos in fixed point, units of 2^-17 (the replica
+// forms that keep a replica in one CTA or cluster, n_osc <= 8192): integer
+// sums are exact and associative, so the totals are the same however the
+// oscillators are split over threads, warps and CTAs, and a warp adds 32
+// values in one redux instruction.  |sum| <= 8192 x 2^17 = 2^30.  The
+// quantisation (<= 2^-18 per value) moves S and C by ~1e-5 at N = 4096,
+// which reaches a phase only through K dt / (2 pi N).
+constexpr float kQuant = 131072.0f;
+constexpr float kInvQuant = 1.0f / 131072.0f;
+
+__device__ __forceinline__ int quant(float v) { return __float2int_rn(v * kQuant); }
+
+__device__ __forceinline__ int2 warp_qsum(int a, int b) {
+  return make_int2(__reduce_add_sync(0xffffffffu, a), __reduce_add_sync(0xffffffffu, b));
+}
+
+__device__ __forceinline__ float2 unquant(int2 v) { return make_float2((float)v.x * kInvQuant, (float)v.y * kInvQuant); }
+
+// Block total of the fixed-point pair; every thread receives it.  `red`
+// alternates between two slots so one barrier per reduction suffices.
+__device__ __forceinline__ float2 block_qsum(int a, int b, int2 *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int2 v = warp_qsum(a, b);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = lane < nw ? red[lane] : make_int2(0, 0);
+  return unquant(warp_qsum(v.x, v.y));
+}
+
 // Blocks of up to 1024 threads hold 1-2 oscillators per thread; larger
 // per-thread counts run in blocks of at most 512 threads (128 registers).
 template <int OPT>
 __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel(const KurArgs A) {
-  __shared__ float2 red[2][32];
+  __shared__ int2 red[2][32];
   const int rep = blockIdx.x;
   const int64_t N = A.N;
   const int64_t base = (int64_t)rep * N;
@@ -101,15 +131,15 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
     for (int s = 0; s < 4; ++s) {
       if (s < s0 || s >= s1) continue;
       float sn[OPT], cs[OPT];
-      float S = 0.0f, C = 0.0f;
+      int S = 0, C = 0;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         sincos_turns(th[k], sn[k], cs[k]);
         if (!valid[k]) sn[k] = cs[k] = 0.0f;
-        S += sn[k];
-        C += cs[k];
+        S += quant(sn[k]);
+        C += quant(cs[k]);
       }
-      float2 sc = block_sum2(S, C, red[slot]);
+      float2 sc = block_qsum(S, C, red[slot]);
       slot ^= 1;
       if (A.M > 0 && sample_ctr == 0) {
         if (threadIdx.x == 0 && A.r_out) {
@@ -120,17 +150,17 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
       }
       if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
       float g1[OPT], sn2[OPT], cs2[OPT];
-      float S2 = 0.0f, C2 = 0.0f;
+      int S2 = 0, C2 = 0;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
         sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
-        S2 += sn2[k];
-        C2 += cs2[k];
+        S2 += quant(sn2[k]);
+        C2 += quant(cs2[k]);
       }
-      sc = block_sum2(S2, C2, red[slot]);
+      sc = block_qsum(S2, C2, red[slot]);
       slot ^= 1;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
@@ -143,17 +173,17 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
   }
   // Final sample at n_end.
   if (A.M > 0) {
-    float S = 0.0f, C = 0.0f;
+    int S = 0, C = 0;
 #pragma unroll
     for (int k = 0; k < OPT; ++k) {
       float sn, cs;
       sincos_turns(th[k], sn, cs);
       if (valid[k]) {
-        S += sn;
-        C += cs;
+        S += quant(sn);
+        C += quant(cs);
       }
     }
-    const float2 sc = block_sum2(S, C, red[slot]);
+    const float2 sc = block_qsum(S, C, red[slot]);
     if (threadIdx.x == 0 && A.r_out) {
       const double Sd = sc.x, Cd = sc.y;
       A.r_out[sample_idx * A.R + rep] = sqrt(Sd * Sd + Cd * Cd) / (double)N;
@@ -178,7 +208,7 @@ template <int OPT>
 __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const KurArgs A) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ float2 slots[2][32];  // [buffer][cluster rank * warps + warp]
+  __shared__ int2 slots[2][32];  // [buffer][cluster rank * warps + warp]
   const int cs = (int)cluster.num_blocks();
   const int crank = (int)cluster.block_rank();
   const int nwarps = blockDim.x >> 5;
@@ -206,16 +236,16 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
   int buf = 0;
   int64_t sample_ctr = 0, sample_idx = 0;
   // cluster-wide (S, C)
-  auto cluster_sum = [&](float S, float C) -> float2 {
-    const float2 part = warp_sum2(S, C);
+  auto cluster_sum = [&](int S, int C) -> float2 {
+    const int2 part = warp_qsum(S, C);
     if (lane < cs) {
-      float2 *dst = cluster.map_shared_rank(&slots[buf][crank * nwarps + warp], lane);
+      int2 *dst = cluster.map_shared_rank(&slots[buf][crank * nwarps + warp], lane);
       *dst = part;
     }
     cluster.sync();
-    const float2 v = lane < nslots ? slots[buf][lane] : make_float2(0.0f, 0.0f);
+    const int2 v = lane < nslots ? slots[buf][lane] : make_int2(0, 0);
     buf ^= 1;
-    return warp_sum2(v.x, v.y);
+    return unquant(warp_qsum(v.x, v.y));
   };
   for (int64_t n = A.n_begin; n < A.n_end;) {
     const int64_t g = n >> 2;
@@ -229,13 +259,13 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
     for (int s = 0; s < 4; ++s) {
       if (s < s0 || s >= s1) continue;
       float sn[OPT], cs_[OPT];
-      float S = 0.0f, C = 0.0f;
+      int S = 0, C = 0;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         sincos_turns(th[k], sn[k], cs_[k]);
         if (!valid[k]) sn[k] = cs_[k] = 0.0f;
-        S += sn[k];
-        C += cs_[k];
+        S += quant(sn[k]);
+        C += quant(cs_[k]);
       }
       float2 sc = cluster_sum(S, C);
       if (A.M > 0 && sample_ctr == 0) {
@@ -247,15 +277,15 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
       }
       if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
       float g1[OPT], sn2[OPT], cs2[OPT];
-      float S2 = 0.0f, C2 = 0.0f;
+      int S2 = 0, C2 = 0;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
         sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
-        S2 += sn2[k];
-        C2 += cs2[k];
+        S2 += quant(sn2[k]);
+        C2 += quant(cs2[k]);
       }
       sc = cluster_sum(S2, C2);
 #pragma unroll
@@ -268,14 +298,14 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
     n = (g + 1) << 2;
   }
   if (A.M > 0) {
-    float S = 0.0f, C = 0.0f;
+    int S = 0, C = 0;
 #pragma unroll
     for (int k = 0; k < OPT; ++k) {
       float sn, c;
       sincos_turns(th[k], sn, c);
       if (valid[k]) {
-        S += sn;
-        C += c;
+        S += quant(sn);
+        C += quant(c);
       }
     }
     const float2 sc = cluster_sum(S, C);
@@ -341,7 +371,7 @@ template <int OPT>
 __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurArgs A) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
-  __shared__ float2 slots[2][32];
+  __shared__ int2 slots[2][32];
   __shared__ __align__(8) uint64_t mbar[2];
   const int cs = (int)cluster.num_blocks();
   const int crank = (int)cluster.block_rank();
@@ -390,15 +420,15 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
   const uint32_t rbar1 = lane < cs ? cluster_map(smem_u32(&mbar[1]), (uint32_t)lane) : 0u;
   uint32_t stage = 0;
   bool failed = false;  // warp-uniform
-  auto cluster_sum = [&](float S, float C) -> float2 {
-    const float2 part = warp_sum2(S, C);
+  auto cluster_sum = [&](int S, int C) -> float2 {
+    const int2 part = warp_qsum(S, C);
     const int b = (int)(stage & 1u);
     const uint32_t parity = (stage >> 1) & 1u;
     const uint32_t bar = smem_u32(&mbar[b]);
     if (lane < cs)
-      asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+      asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.s32 [%0], {%1, %2}, [%3];" ::"r"(
                        b ? rslot1 : rslot0),
-                   "f"(part.x), "f"(part.y), "r"(b ? rbar1 : rbar0)
+                   "r"(part.x), "r"(part.y), "r"(b ? rbar1 : rbar0)
                    : "memory");
     const bool ok = mbar_wait_bounded(bar, parity);
     if (__any_sync(0xffffffffu, !ok)) {
@@ -407,9 +437,9 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
     }
     if (threadIdx.x == 0 && ok)  // arm this buffer's next phase (stage + 2)
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    const float2 v = lane < nslots ? slots[b][lane] : make_float2(0.0f, 0.0f);
+    const int2 v = lane < nslots ? slots[b][lane] : make_int2(0, 0);
     ++stage;
-    return warp_sum2(v.x, v.y);
+    return unquant(warp_qsum(v.x, v.y));
   };
   int64_t sample_ctr = 0, sample_idx = 0;
   for (int64_t n = A.n_begin; n < A.n_end && !failed;) {
@@ -424,13 +454,13 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
     for (int s = 0; s < 4; ++s) {
       if (s < s0 || s >= s1 || failed) continue;
       float sn[OPT], cs_[OPT];
-      float S = 0.0f, C = 0.0f;
+      int S = 0, C = 0;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         sincos_turns(th[k], sn[k], cs_[k]);
         if (!valid[k]) sn[k] = cs_[k] = 0.0f;
-        S += sn[k];
-        C += cs_[k];
+        S += quant(sn[k]);
+        C += quant(cs_[k]);
       }
       float2 sc = cluster_sum(S, C);
       if (A.M > 0 && sample_ctr == 0) {
@@ -442,15 +472,15 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
       }
       if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
       float g1[OPT], sn2[OPT], cs2[OPT];
-      float S2 = 0.0f, C2 = 0.0f;
+      int S2 = 0, C2 = 0;
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
         sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
-        S2 += sn2[k];
-        C2 += cs2[k];
+        S2 += quant(sn2[k]);
+        C2 += quant(cs2[k]);
       }
       sc = cluster_sum(S2, C2);
 #pragma unroll
@@ -463,14 +493,14 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
     n = (g + 1) << 2;
   }
   if (A.M > 0 && !failed) {
-    float S = 0.0f, C = 0.0f;
+    int S = 0, C = 0;
 #pragma unroll
     for (int k = 0; k < OPT; ++k) {
       float sn, c;
       sincos_turns(th[k], sn, c);
       if (valid[k]) {
-        S += sn;
-        C += c;
+        S += quant(sn);
+        C += quant(c);
       }
     }
     const float2 sc = cluster_sum(S, C);

@@ -139,3 +139,20 @@ def test_uniform_size_r_of_t_within_3se():
     late = slice(S // M // 2, None)
     print("r late mean %.4f se %.4f" % (obs["mean"][late].mean(), obs["se"][late].mean()))
     assert 0.0 < obs["mean"][-1] < 1.0
+
+
+def test_meanfield_shapes_are_bit_identical():
+    # the sums of sin and cos are exact fixed-point integers, so every way of
+    # splitting a replica over threads, warps, CTAs and clusters gives the
+    # same totals and therefore the same trajectory bit for bit
+    N, R, steps, M = 4096, 3, 203, 50
+    w = inputs.kuramoto_uniform(n_osc=N, replicas=R, seed=21)
+    shapes = [dict(block_threads=256), dict(block_threads=512), dict(block_threads=512, cluster_ctas=2),
+              dict(block_threads=256, cluster_ctas=4, flags=AX), dict(block_threads=128, cluster_ctas=8)]
+    runs = []
+    for shp in shapes:
+        ens = _ens(sde.SDE_KURAMOTO_MEANFIELD, N, R, 2.0, 0.05, 0.01, 5, M, **shp)
+        runs.append(kur_run(ens, w["phi0"], w["omega"], 0, steps))
+    for phig, rg, _ in runs[1:]:
+        assert np.array_equal(phig, runs[0][0])
+        assert np.array_equal(rg, runs[0][1])
