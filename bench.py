@@ -492,7 +492,7 @@ def run_ours(args, rank, world, device):
         "ms_per_step": ms,
         "higher_is_better": True,
         "scaling": "weak",
-        "vs_baseline": None,
+        "vs_baseline": vs_paper(args, sde_dist.aggregate_rate(units, world, ms * 1e-3)),
         "dtype": "f64" if args.workload == "fig2-fp64" else "f32 (FP64 reductions)",
         "data": "synthetic (seeded; inputs.py)",
         "config": cfg,
@@ -509,6 +509,19 @@ def run_ours(args, rank, world, device):
     }
     res.update(extra)
     return res, ens
+
+
+# The paper's own figures for the exact workloads it timed (NVIDIA Tesla C1060,
+# another machine: context, not a target): the Fig. 2 ensemble, 2^19 paths x
+# 2e5 steps, in 20 s single precision and 13 min double precision.
+PAPER_RATE = {"fig2": 2 ** 19 * 2e5 / 20.0, "fig2-fp64": 2 ** 19 * 2e5 / (13 * 60.0)}
+
+
+def vs_paper(args, value):
+    ref = PAPER_RATE.get(args.workload)
+    if ref is None or args.euler or args.schedule == "plain":
+        return None
+    return value / ref
 
 
 def host_cores():
