@@ -299,7 +299,7 @@ sde_status sde_box_muller(const uint32_t *ctr_dev, uint64_t seed, float *z_dev, 
  * aligned), with the uniforms of sde_box_muller.  variant 0: the transform
  * the Kuramoto and surrogate kernels use (accurate logf, sin/cos of the
  * fixed-point angle); variant 1: the Josephson kernels' (angle from a
- * 256-entry table plus angle addition; ln u0 from the hardware base-2
+ * 1024-entry table plus angle addition; ln u0 from the hardware base-2
  * logarithm: the radius is within ~5e-4 absolute, and within ~1e-7
  * relative for u0 well below 1).  For exhaustive checks of both.
  */

@@ -253,7 +253,7 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
   // drive table cos(2 pi k / P), k = 0 .. P + 3 (four entries of padding
   // repeat the start of the period), 16-byte aligned
   extern __shared__ float4 drive_s4[];
-  __shared__ float2 bm_tab[256];  // Box-Muller angle table
+  __shared__ float2 bm_tab[kBmTable];  // Box-Muller angle table
   float *drive_s = reinterpret_cast<float *>(drive_s4);
   for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x) drive_s[i] = A.drive[i % A.P];
   fill_bm_table(bm_tab);
@@ -373,7 +373,7 @@ __global__ void box_muller_fill_kernel(const uint4 *ctr, uint2 key, float4 *z, i
 // library's default transform, 1 the Josephson kernels' (table angle,
 // hardware logarithm).
 __global__ void box_muller_words_kernel(const uint2 *w, int64_t n, int variant, float2 *z) {
-  __shared__ float2 tab[256];
+  __shared__ float2 tab[kBmTable];
   fill_bm_table(tab);
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -511,7 +511,7 @@ struct NoallocArgs {
 // unit decomposition as the plain schedule with one path per thread.
 __global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
   extern __shared__ float4 drive_s4[];
-  __shared__ float2 bm_tab[256];
+  __shared__ float2 bm_tab[kBmTable];
   float *drive_s = reinterpret_cast<float *>(drive_s4);
   const double dt = 2.0 * 3.14159265358979323846 / (A.p.omega * (double)A.P);
   for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x)

@@ -132,9 +132,9 @@ __device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uin
 // Box-Muller of the Josephson kernels, two shortcuts against box_muller:
 //  * the angle's sine and cosine from a table: the angle 2 pi u1,
 //    u1 = (j + 1) 2^-24 with j = w1 >> 8, is split into the table angle
-//    2 pi q / 256 (q = the top 8 bits of j) and a remainder
-//    b = 2 pi ((j mod 2^16) + 1) 2^-24 in (0, 2 pi / 256]; sin b = b - b^3/6
-//    and cos b = 1 - b^2/2 (the next terms are below 1.5e-8), and the
+//    2 pi q / 1024 (q = the top 10 bits of j) and a remainder
+//    b = 2 pi ((j mod 2^14) + 1) 2^-24 in (0, 2 pi / 1024]; sin b = b and
+//    cos b = 1 - b^2/2 (the next terms are below 4e-8), and the
 //    angle-addition formulas combine them with the table entry (within
 //    about 1e-7 of the exact values);
 //  * ln u0 from the hardware base-2 logarithm (lg2.approx, one instruction)
@@ -143,12 +143,14 @@ __device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uin
 //    u0 -> 1 (radius -> 0); the radius error stays below ~5e-4 everywhere
 //    (the bound the tests check on all 2^24 values of u0).  A slightly
 //    positive log of a u0 just below 1 is clamped to a zero radius.
-// tab[q] = (cos, sin)(2 pi q / 256), q = 0 .. 255, filled by fill_bm_table
-// (shared memory of the calling kernel).
+// tab[q] = (cos, sin)(2 pi q / 1024), q = 0 .. 1023, filled by fill_bm_table
+// (shared memory of the calling kernel, 8 KB).
+constexpr int kBmTable = 1024;
+
 __device__ __forceinline__ void fill_bm_table(float2 *tab) {
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+  for (int q = threadIdx.x; q < kBmTable; q += blockDim.x) {
     float sn, cs;
-    sincospif((float)q * 0.0078125f, &sn, &cs);  // q / 128
+    sincospif((float)q * 0.001953125f, &sn, &cs);  // q / 512
     tab[q] = make_float2(cs, sn);
   }
 }
@@ -159,13 +161,11 @@ __device__ __forceinline__ void box_muller_tab(uint32_t w0, uint32_t w1, const f
   float l2;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(u0));
   const float rho = radius(fmaxf(-1.38629436111989061883f * l2, 0.0f));  // -2 ln 2 log2(u0)
-  const float2 t = tab[w1 >> 24];
-  const float b = fmaf((float)((w1 >> 8) & 0xFFFFu), 3.7450702829239308e-7f, 3.7450702829239308e-7f);  // 2 pi 2^-24
-  const float b2 = b * b;
-  const float cb = fmaf(-0.5f, b2, 1.0f);
-  const float sb = fmaf(b * b2, -0.16666667f, b);
-  z0 = rho * fmaf(t.x, cb, -t.y * sb);
-  z1 = rho * fmaf(t.y, cb, t.x * sb);
+  const float2 t = tab[w1 >> 22];
+  const float b = fmaf((float)((w1 >> 8) & 0x3FFFu), 3.7450702829239308e-7f, 3.7450702829239308e-7f);  // 2 pi 2^-24
+  const float cb = fmaf(-0.5f * b, b, 1.0f);
+  z0 = rho * fmaf(t.x, cb, -t.y * b);
+  z1 = rho * fmaf(t.y, cb, t.x * b);
 }
 
 // gauss4 with round keys and the Box-Muller angle table.
