@@ -419,7 +419,7 @@ def run_ours(args, rank, world, device):
         t0 = time.perf_counter()
         step_e2e()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = statistics.median(e2e_ms) if e2e_ms else float("nan")
+    e2e = statistics.median(e2e_ms) if e2e_ms else None
 
     extra = {}
     if args.workload == "fig2":
@@ -501,7 +501,7 @@ def run_ours(args, rank, world, device):
                      "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "flop_model": flop_note,
                      "peak_source": peak_note, "kernel_ms_per_launch": k_ms},
-        "e2e": {"value": units * world / (e2e * 1e-3), "unit": metric.split("/")[0] + "/s",
+        "e2e": {"value": units * world / (e2e * 1e-3) if e2e else None, "unit": metric.split("/")[0] + "/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,

@@ -336,6 +336,7 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
   }
   c->total_paths = off;
   SDE_CHECK_ARG(off < (1ll << 40), "total paths too large");
+  SDE_CUDA_TRY(jj_configure());
 
   sde_jj_point *pts = nullptr;
   int64_t *steps = nullptr, *offs = nullptr, *paths = nullptr;

@@ -82,6 +82,7 @@ cudaError_t jj_prepare(const sde_jj_point *points_dev, int n_points, int P, cons
                        float *drive_dev, cudaStream_t s);
 cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaStream_t s);
 int jj_max_blocks_per_sm(int ilp, int block, int P);
+cudaError_t jj_configure();  // once per process, before the first launch (not under capture)
 cudaError_t jj_finalize(const JJConsts *consts, const int2 *point_range, int n_points,
                         const Moments *partials, int64_t n_end, sde_obs_row *obs, cudaStream_t s);
 

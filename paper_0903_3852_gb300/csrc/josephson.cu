@@ -85,9 +85,24 @@ __device__ __forceinline__ void jj_wrap(float &x, int &w) {
   w += (int)fl;
 }
 
+// Drive tables: the shared cos(2 pi k / P) table (P + 4 entries) and, for
+// P <= kWarpTableMaxP, one table of a cos + f per warp, each padded to a
+// multiple of 4 floats.
+constexpr int kWarpTableMaxP = 1020;
+constexpr int kJJMaxBlock = 512;  // the largest block any Josephson launch uses
+
+__host__ __device__ inline int jj_table_stride(int P) { return (P + 4 + 3) & ~3; }
+
+__host__ inline size_t jj_smem_bytes(int P, int block) {
+  const int pp = jj_table_stride(P);
+  return sizeof(float) * (size_t)pp * (P <= kWarpTableMaxP ? 1 + block / 32 : 1);
+}
+
 // Advance ILP paths over the steps [n0, n1).  `k` is the drive-table index
 // of step n0 (n0 mod P) and is updated.
-template <int ILP, bool ACC, bool EM = false>
+// SCALED: `drive` holds a cos(2 pi k / P) + f for this point (a per-warp or
+// per-point table), else cos(2 pi k / P) and the drive term is formed here.
+template <int ILP, bool ACC, bool EM = false, bool SCALED = false>
 __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float (&v)[ILP],
                                            double (&vs)[ILP], const JJConsts &c,
                                            const float *__restrict__ drive, int P, int &k,
@@ -111,17 +126,17 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
       if ((P & 3) == 0) {
         // k is a multiple of 4 here; the table is padded by 4 entries
         const float4 d = *reinterpret_cast<const float4 *>(drive + k);
-        e[0] = fmaf(c.a, d.x, c.f);
-        e[1] = fmaf(c.a, d.y, c.f);
-        e[2] = fmaf(c.a, d.z, c.f);
-        e[3] = fmaf(c.a, d.w, c.f);
-        e[4] = fmaf(c.a, drive[k + 4], c.f);
+        e[0] = SCALED ? d.x : fmaf(c.a, d.x, c.f);
+        e[1] = SCALED ? d.y : fmaf(c.a, d.y, c.f);
+        e[2] = SCALED ? d.z : fmaf(c.a, d.z, c.f);
+        e[3] = SCALED ? d.w : fmaf(c.a, d.w, c.f);
+        e[4] = SCALED ? drive[k + 4] : fmaf(c.a, drive[k + 4], c.f);
         k += 4;
         if (k == P) k = 0;
       } else {
 #pragma unroll
         for (int s = 0; s < 5; ++s) {
-          e[s] = fmaf(c.a, drive[k], c.f);
+          e[s] = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
           if (s < 4) k = (k + 1 == P) ? 0 : k + 1;
         }
       }
@@ -134,9 +149,9 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
       for (int s = 0; s < 4; ++s) {
         const int64_t n = base + s;
         if (n >= n0 && n < n1) {
-          const float e0 = fmaf(c.a, drive[k], c.f);
+          const float e0 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
           k = (k + 1 == P) ? 0 : k + 1;
-          const float e1 = fmaf(c.a, drive[k], c.f);
+          const float e1 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
 #pragma unroll
           for (int i = 0; i < ILP; ++i) jj_step<ACC, EM>(x[i], v[i], acc[i], z[i][s], c, e0, e1);
         }
@@ -167,8 +182,8 @@ __device__ __forceinline__ double warp_sum(double a) {
 }
 
 template <int ILP, bool EM>
-__device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, const float2 *bm_tab,
-                                        int lane) {
+__device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, float *wtab,
+                                        const float2 *bm_tab, int lane) {
   const JJUnit un = A.units[u];
   const JJConsts c = A.consts[un.point];
   const PhiloxKeys &key = A.keys;
@@ -203,9 +218,19 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
   if (nb < ne) {
     int k = (int)(nb % A.P);
     const int64_t split = ne < c.wstart ? ne : c.wstart;
-    jj_segment<ILP, false, EM>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point, bm_tab);
-    jj_segment<ILP, true, EM>(x, w, v, vs, c, drive, A.P, k, nb > c.wstart ? nb : c.wstart, ne, key, pid,
-                              (uint32_t)un.point, bm_tab);
+    const int64_t w0 = nb > c.wstart ? nb : c.wstart;
+    if (wtab) {
+      // this warp's copy of the drive term a cos(2 pi k / P) + f of the unit's point
+      for (int q = lane; q < A.P + 4; q += 32) wtab[q] = fmaf(c.a, drive[q], c.f);
+      __syncwarp();
+      jj_segment<ILP, false, EM, true>(x, w, v, vs, c, wtab, A.P, k, nb, split, key, pid, (uint32_t)un.point,
+                                       bm_tab);
+      jj_segment<ILP, true, EM, true>(x, w, v, vs, c, wtab, A.P, k, w0, ne, key, pid, (uint32_t)un.point, bm_tab);
+      __syncwarp();  // the table is rewritten for the warp's next unit
+    } else {
+      jj_segment<ILP, false, EM>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point, bm_tab);
+      jj_segment<ILP, true, EM>(x, w, v, vs, c, drive, A.P, k, w0, ne, key, pid, (uint32_t)un.point, bm_tab);
+    }
   }
   bool bad = false;
 #pragma unroll
@@ -260,6 +285,9 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
+  // per-warp tables of the drive term (P <= kWarpTableMaxP), 16-byte aligned
+  const int pp = jj_table_stride(A.P);
+  float *wtab = A.P <= kWarpTableMaxP ? drive_s + pp * (1 + (threadIdx.x >> 5)) : nullptr;
   if (A.queue) {
     // Persistent: warps pull units from the longest-first work list.
     for (;;) {
@@ -267,11 +295,11 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
       if (lane == 0) u = (int)atomicAdd(A.queue, 1u) + A.unit_begin;
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= A.unit_end) break;
-      jj_unit<ILP, EM>(A, u, drive_s, bm_tab, lane);
+      jj_unit<ILP, EM>(A, u, drive_s, wtab, bm_tab, lane);
     }
   } else {
     const int u = A.unit_begin + blockIdx.x * warps + (threadIdx.x >> 5);
-    if (u < A.unit_end) jj_unit<ILP, EM>(A, u, drive_s, bm_tab, lane);
+    if (u < A.unit_end) jj_unit<ILP, EM>(A, u, drive_s, wtab, bm_tab, lane);
   }
 }
 
@@ -415,7 +443,7 @@ cudaError_t jj_prepare(const sde_jj_point *points_dev, int n_points, int P, cons
 
 // `ilp` encodes the variant: 1, 2 = paths per thread; +10 = registers capped at 64.
 cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(float) * (size_t)(a.P + 4);
+  const size_t smem = jj_smem_bytes(a.P, block);
   switch (ilp) {
     case 1: jj_kernel<1><<<grid, block, smem, s>>>(a); break;
     case 2: jj_kernel<2><<<grid, block, smem, s>>>(a); break;
@@ -435,9 +463,25 @@ int jj_max_blocks_per_sm(int ilp, int block, int P) {
   int nb = 0;
   void *k = jj_kernel_ptr(ilp);
   if (!k) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, sizeof(float) * (P + 4)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, jj_smem_bytes(P, block)) != cudaSuccess)
     return 0;
   return nb;
+}
+
+// The dynamic shared memory limit is a per-function maximum shared by every
+// launch in the process, so it is raised once, to what the largest table
+// layout (P = kWarpTableMaxP, kJJMaxBlock threads) needs, and never lowered.
+cudaError_t jj_configure() {
+  static const cudaError_t status = [] {
+    const int smem = (int)jj_smem_bytes(kWarpTableMaxP, kJJMaxBlock);
+    const int variants[] = {1, 2, 11, 12, 101, 102, 111, 112};
+    for (int v : variants) {
+      const cudaError_t e = cudaFuncSetAttribute(jj_kernel_ptr(v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }();
+  return status;
 }
 
 cudaError_t jj_finalize(const JJConsts *consts, const int2 *point_range, int n_points,
