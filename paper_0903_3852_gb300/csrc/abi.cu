@@ -44,7 +44,7 @@ struct sde_ctx {
   JJConsts *consts = nullptr;
   float *drive = nullptr;
   int64_t *offsets_dev = nullptr, *paths_dev = nullptr;  // per point (histograms)
-  JJUnitList units[3];  // indexed by ILP (1, 2)
+  JJUnitList units[5];  // indexed by paths per thread (1, 2, 4)
   Moments *partials = nullptr;
   uint32_t *queue = nullptr;
   int block = 0, ilp = 0;
@@ -133,7 +133,7 @@ sde_status build_units(sde_ctx *c, int ilp) {
   return SDE_OK;
 }
 
-// Launch variants: 1, 2 = paths per thread; 11, 12 = the same with registers
+// Launch variants: 1, 2, 4 = paths per thread; 11, 12 = 1, 2 with registers
 // capped at 64.  The work list depends on the paths per thread only.
 int paths_per_thread(int variant) { return variant % 10; }
 
@@ -224,7 +224,7 @@ sde_status jj_autotune(sde_ctx *c) {
   else if (c->cfg.schedule == SDE_SCHED_PLAIN)
     il.push_back(1);  // the per-path kernel of Alg. 1: one thread per path
   else
-    il = {1, 2, 11, 12};
+    il = {1, 2, 4, 12};
   // Euler-Maruyama kernels carry the variant code + 100
   const int scheme = (c->cfg.flags & SDE_FLAG_EULER) ? 100 : 0;
   for (int b : bl)
@@ -311,8 +311,8 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
                      cfg->block_threads % 32 == 0),
                 "block_threads must be 0 or a multiple of 32 in [32, 512]");
   SDE_CHECK_ARG(cfg->paths_per_thread == 0 || cfg->paths_per_thread == 1 || cfg->paths_per_thread == 2 ||
-                    cfg->paths_per_thread == 11 || cfg->paths_per_thread == 12,
-                "paths_per_thread must be 0, 1, 2, 11 or 12");
+                    cfg->paths_per_thread == 4 || cfg->paths_per_thread == 11 || cfg->paths_per_thread == 12,
+                "paths_per_thread must be 0, 1, 2, 4, 11 or 12");
   c->n_points = cfg->n_points;
   c->P = cfg->steps_per_period;
   c->paths.resize(c->n_points);
@@ -358,7 +358,7 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
   c->paths_dev = paths;
 
   int32_t max_units = 0;
-  for (int ilp = 1; ilp <= 2; ++ilp) {
+  for (int ilp : {1, 2, 4}) {
     sde_status st = build_units(c, ilp);
     if (st != SDE_OK) return st;
     max_units = std::max(max_units, c->units[ilp].n_units);

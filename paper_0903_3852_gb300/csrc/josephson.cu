@@ -78,6 +78,68 @@ __device__ __forceinline__ void jj_step(float &x, float &v, float &acc, float z,
   if (ACC) acc += v;
 }
 
+// The same step for two paths at once on packed FP32 pairs (Blackwell's
+// two-wide FMA, add and multiply, rounded like fmaf and +), so one
+// instruction advances both paths of a thread.  Same operations in the same
+// order as jj_force / jj_step: the results are bit-identical.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ float2 jj_force2(float2 x, float2 A) {
+  // -|r| by setting the sign bit; rint is symmetric, so -rint(x) = rint(-x)
+  const float2 r = __fadd2_rn(x, make_float2(rintf(-x.x), rintf(-x.y)));
+  const float2 nr = make_float2(__int_as_float(__float_as_int(r.x) | 0x80000000),
+                                __int_as_float(__float_as_int(r.y) | 0x80000000));
+  const float2 b = __fadd2_rn(f2(0.25f), nr);
+  const float2 s = __fmul2_rn(b, b);
+  float2 p = __ffma2_rn(f2(-2.484164429e+02f), s, f2(4.809764709e+02f));
+  p = __ffma2_rn(p, s, f2(-5.127142334e+02f));
+  p = __ffma2_rn(p, s, f2(2.597572937e+02f));
+  p = __ffma2_rn(p, s, f2(-3.947841644e+01f));
+  return __ffma2_rn(b, p, A);
+}
+
+template <bool ACC, bool EM>
+__device__ __forceinline__ void jj_step2(float2 &x, float2 &v, float2 &acc, float2 z, const JJConsts &c, float e0,
+                                         float e1) {
+  const float2 vn = __ffma2_rn(f2(c.s), z, v);
+  const float2 F1 = jj_force2(x, __ffma2_rn(f2(-c.gamma), v, f2(e0)));
+  if (EM) {
+    x = __ffma2_rn(f2(c.dt), v, x);
+    v = __ffma2_rn(f2(c.dt), F1, vn);
+    if (ACC) acc = __fadd2_rn(acc, v);
+    return;
+  }
+  const float2 xt = __ffma2_rn(f2(c.dt), v, x);
+  const float2 vt = __ffma2_rn(f2(c.dt), F1, vn);
+  const float2 F2 = jj_force2(xt, __ffma2_rn(f2(-c.gamma), vt, f2(e1)));
+  x = __ffma2_rn(f2(c.h), __fadd2_rn(v, vt), x);
+  v = __ffma2_rn(f2(c.h), __fadd2_rn(F1, F2), vn);
+  if (ACC) acc = __fadd2_rn(acc, v);
+}
+
+// Steps s of a group for all ILP paths (packed pairs where ILP is even).
+template <int ILP, bool ACC, bool EM>
+__device__ __forceinline__ void jj_steps(float (&x)[ILP], float (&v)[ILP], float (&acc)[ILP],
+                                         const float (&z)[ILP][4], int s, const JJConsts &c, float e0, float e1) {
+  if constexpr (ILP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < ILP; i += 2) {
+      float2 X = make_float2(x[i], x[i + 1]), V = make_float2(v[i], v[i + 1]);
+      float2 S = make_float2(acc[i], acc[i + 1]);
+      jj_step2<ACC, EM>(X, V, S, make_float2(z[i][s], z[i + 1][s]), c, e0, e1);
+      x[i] = X.x;
+      x[i + 1] = X.y;
+      v[i] = V.x;
+      v[i + 1] = V.y;
+      acc[i] = S.x;
+      acc[i + 1] = S.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) jj_step<ACC, EM>(x[i], v[i], acc[i], z[i][s], c, e0, e1);
+  }
+}
+
 // Fold x back into [0, 1), counting whole turns in w.
 __device__ __forceinline__ void jj_wrap(float &x, int &w) {
   const float fl = floorf(x);
@@ -141,9 +203,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
         }
       }
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int i = 0; i < ILP; ++i) jj_step<ACC, EM>(x[i], v[i], acc[i], z[i][s], c, e[s], e[s + 1]);
+      for (int s = 0; s < 4; ++s) jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e[s], e[s + 1]);
     } else {
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
@@ -152,8 +212,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
           const float e0 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
           k = (k + 1 == P) ? 0 : k + 1;
           const float e1 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
-#pragma unroll
-          for (int i = 0; i < ILP; ++i) jj_step<ACC, EM>(x[i], v[i], acc[i], z[i][s], c, e0, e1);
+          jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e0, e1);
         }
       }
     }
@@ -316,6 +375,14 @@ __global__ void __launch_bounds__(512, 2) jj_kernel_cap64(const JJLaunchArgs A) 
   jj_kernel_body<ILP, EM>(A);
 }
 
+// Packed-pair kernels (2 or 4 paths per thread) at the fewest registers that
+// hold them without spills: 72 for one pair (28 warps per SM in blocks of
+// 128), 88 for two (20 warps, each with two independent pairs in flight).
+template <int ILP, bool EM = false>
+__global__ void __maxnreg__(ILP == 2 ? 72 : 88) jj_kernel_packed(const JJLaunchArgs A) {
+  jj_kernel_body<ILP, EM>(A);
+}
+
 __global__ void jj_prepare_kernel(const sde_jj_point *pts, int n_points, int P,
                                   const int64_t *steps, const int64_t *offsets,
                                   const int64_t *paths, JJConsts *out, float *drive) {
@@ -419,11 +486,13 @@ __global__ void box_muller_words_kernel(const uint2 *w, int64_t n, int variant, 
 void *jj_kernel_ptr(int variant) {
   switch (variant) {
     case 1: return (void *)jj_kernel<1>;
-    case 2: return (void *)jj_kernel<2>;
+    case 2: return (void *)jj_kernel_packed<2>;
+    case 4: return (void *)jj_kernel_packed<4>;
     case 11: return (void *)jj_kernel_cap64<1>;
     case 12: return (void *)jj_kernel_cap64<2>;
     case 101: return (void *)jj_kernel<1, true>;
-    case 102: return (void *)jj_kernel<2, true>;
+    case 102: return (void *)jj_kernel_packed<2, true>;
+    case 104: return (void *)jj_kernel_packed<4, true>;
     case 111: return (void *)jj_kernel_cap64<1, true>;
     case 112: return (void *)jj_kernel_cap64<2, true>;
   }
@@ -441,17 +510,20 @@ cudaError_t jj_prepare(const sde_jj_point *points_dev, int n_points, int P, cons
   return cudaGetLastError();
 }
 
-// `ilp` encodes the variant: 1, 2 = paths per thread; +10 = registers capped at 64.
+// `ilp` encodes the variant: 1, 2, 4 = paths per thread; +10 = registers capped at 64
+// (1 and 2 only); +100 = Euler-Maruyama.
 cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaStream_t s) {
   const size_t smem = jj_smem_bytes(a.P, block);
   switch (ilp) {
     case 1: jj_kernel<1><<<grid, block, smem, s>>>(a); break;
-    case 2: jj_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 2: jj_kernel_packed<2><<<grid, block, smem, s>>>(a); break;
+    case 4: jj_kernel_packed<4><<<grid, block, smem, s>>>(a); break;
     case 11: jj_kernel_cap64<1><<<grid, block, smem, s>>>(a); break;
     case 12: jj_kernel_cap64<2><<<grid, block, smem, s>>>(a); break;
     // Euler-Maruyama variants: the code + 100
     case 101: jj_kernel<1, true><<<grid, block, smem, s>>>(a); break;
-    case 102: jj_kernel<2, true><<<grid, block, smem, s>>>(a); break;
+    case 102: jj_kernel_packed<2, true><<<grid, block, smem, s>>>(a); break;
+    case 104: jj_kernel_packed<4, true><<<grid, block, smem, s>>>(a); break;
     case 111: jj_kernel_cap64<1, true><<<grid, block, smem, s>>>(a); break;
     case 112: jj_kernel_cap64<2, true><<<grid, block, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
@@ -474,7 +546,7 @@ int jj_max_blocks_per_sm(int ilp, int block, int P) {
 cudaError_t jj_configure() {
   static const cudaError_t status = [] {
     const int smem = (int)jj_smem_bytes(kWarpTableMaxP, kJJMaxBlock);
-    const int variants[] = {1, 2, 11, 12, 101, 102, 111, 112};
+    const int variants[] = {1, 2, 4, 11, 12, 101, 102, 104, 111, 112};
     for (int v : variants) {
       const cudaError_t e = cudaFuncSetAttribute(jj_kernel_ptr(v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;

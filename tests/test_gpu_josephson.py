@@ -37,7 +37,8 @@ def _oracle_paths(pt, x0, v0, n0, n1, total, seed, point=0, path0=0, vsum=None):
 
 
 SHAPES = [(sde.SDE_SCHED_PERSISTENT, 0, 1), (sde.SDE_SCHED_PERSISTENT, 0, 2),
-          (sde.SDE_SCHED_PLAIN, 0, 1), (sde.SDE_SCHED_PERSISTENT, 64, 2)]
+          (sde.SDE_SCHED_PLAIN, 0, 1), (sde.SDE_SCHED_PERSISTENT, 64, 2),
+          (sde.SDE_SCHED_PERSISTENT, 128, 4), (sde.SDE_SCHED_PLAIN, 256, 4)]
 
 
 @pytest.mark.parametrize("schedule,block,ilp", SHAPES)
@@ -158,7 +159,7 @@ def test_small_sweep_pathwise_and_rows():
     paths = [0, 1, 31, 33, 64, 100, 257]
     steps = [50, 3, 0, 1001, 2002, 1500, 777]
     w = inputs.josephson_custom(pts, paths, steps, seed=9)
-    for ilp in (1, 2):
+    for ilp in (1, 2, 4):
         ens = _ens(pts, paths, steps, seed=9, paths_per_thread=ilp)
         xg, vg, wg, fg, sg, obs = jj_run(ens, w["x0"], w["v0"], 0, max(steps))
         off = 0
@@ -177,6 +178,26 @@ def test_small_sweep_pathwise_and_rows():
                 assert abs(row["mean"] - mo) <= 1e-5 * max(1, abs(mo))
             assert abs(row["t"] - S * 2 * math.pi / (pt["omega"] * P)) < 1e-9
             off += npk
+
+
+def test_launch_variants_are_bit_identical():
+    # one path per thread (scalar FP32) and pairs of paths on packed FP32x2
+    # instructions (2 and 4 per thread, capped registers) perform the same
+    # roundings in the same order: the states and sums agree bit for bit
+    pts = [dict(FIG2, f=0.02 * i) for i in range(5)]
+    paths = [1, 40, 64, 129, 300]
+    steps = [1001, 2000, 7, 1500, 998]
+    w = inputs.josephson_custom(pts, paths, steps, seed=4)
+    ref = None
+    for ilp in (1, 11, 2, 12, 4):
+        ens = _ens(pts, paths, steps, seed=4, paths_per_thread=ilp)
+        out = jj_run(ens, w["x0"], w["v0"], 0, max(steps))
+        got = [np.asarray(a) for a in out[:5]]  # per path: x, v, w, x mod 1, window sum
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), ilp
 
 
 def test_full_sweep_at_bench_size_sampled_points():
