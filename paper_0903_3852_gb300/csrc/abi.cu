@@ -257,7 +257,7 @@ sde_status jj_autotune(sde_ctx *c) {
     r.n_begin = 0;
     int64_t max_steps = 0;
     for (auto S : c->steps) max_steps = std::max(max_steps, S);
-    r.n_end = std::min<int64_t>(max_steps, 768);
+    r.n_end = std::min<int64_t>(max_steps, 2048);
     r.x_in_dev = x;
     r.v_in_dev = v;
     r.x_out_dev = x;

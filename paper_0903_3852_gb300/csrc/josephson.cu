@@ -177,50 +177,56 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
   for (int i = 0; i < ILP; ++i) acc[i] = 0.0f;
   // group indices fit in 32 bits: steps are at most 2^33
   const uint32_t g0 = (uint32_t)(n0 >> 2), g1 = (uint32_t)((n1 - 1) >> 2);
-  for (uint32_t g = g0; g <= g1; ++g) {
-    float z[ILP][4];
+  // Blocks of 16 groups (64 steps) aligned to absolute step indices; the
+  // FP32 partial sums are flushed after each block, outside the group loop,
+  // so the FP64 adds run once per 64 steps.
+  for (uint32_t gb = g0; gb <= g1; gb = (gb | 15u) + 1u) {
+    const uint32_t ge = (gb | 15u) < g1 ? (gb | 15u) : g1;
+    for (uint32_t g = gb; g <= ge; ++g) {
+      float z[ILP][4];
 #pragma unroll
-    for (int i = 0; i < ILP; ++i) gauss4_tab(g, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
-    const int64_t base = (int64_t)g << 2;
-    if (base >= n0 && base + 4 <= n1) {
-      // full group: drive values at t_{4g} .. t_{4g+4}
-      float e[5];
-      if ((P & 3) == 0) {
-        // k is a multiple of 4 here; the table is padded by 4 entries
-        const float4 d = *reinterpret_cast<const float4 *>(drive + k);
-        e[0] = SCALED ? d.x : fmaf(c.a, d.x, c.f);
-        e[1] = SCALED ? d.y : fmaf(c.a, d.y, c.f);
-        e[2] = SCALED ? d.z : fmaf(c.a, d.z, c.f);
-        e[3] = SCALED ? d.w : fmaf(c.a, d.w, c.f);
-        e[4] = SCALED ? drive[k + 4] : fmaf(c.a, drive[k + 4], c.f);
-        k += 4;
-        if (k == P) k = 0;
+      for (int i = 0; i < ILP; ++i) gauss4_tab(g, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
+      const int64_t base = (int64_t)g << 2;
+      if (base >= n0 && base + 4 <= n1) {
+        // full group: drive values at t_{4g} .. t_{4g+4}
+        float e[5];
+        if ((P & 3) == 0) {
+          // k is a multiple of 4 here; the table is padded by 4 entries
+          const float4 d = *reinterpret_cast<const float4 *>(drive + k);
+          e[0] = SCALED ? d.x : fmaf(c.a, d.x, c.f);
+          e[1] = SCALED ? d.y : fmaf(c.a, d.y, c.f);
+          e[2] = SCALED ? d.z : fmaf(c.a, d.z, c.f);
+          e[3] = SCALED ? d.w : fmaf(c.a, d.w, c.f);
+          e[4] = SCALED ? drive[k + 4] : fmaf(c.a, drive[k + 4], c.f);
+          k += 4;
+          if (k == P) k = 0;
+        } else {
+#pragma unroll
+          for (int s = 0; s < 5; ++s) {
+            e[s] = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
+            if (s < 4) k = (k + 1 == P) ? 0 : k + 1;
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e[s], e[s + 1]);
       } else {
 #pragma unroll
-        for (int s = 0; s < 5; ++s) {
-          e[s] = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
-          if (s < 4) k = (k + 1 == P) ? 0 : k + 1;
+        for (int s = 0; s < 4; ++s) {
+          const int64_t n = base + s;
+          if (n >= n0 && n < n1) {
+            const float e0 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
+            k = (k + 1 == P) ? 0 : k + 1;
+            const float e1 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
+            jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e0, e1);
+          }
         }
       }
 #pragma unroll
-      for (int s = 0; s < 4; ++s) jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e[s], e[s + 1]);
-    } else {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int64_t n = base + s;
-        if (n >= n0 && n < n1) {
-          const float e0 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
-          k = (k + 1 == P) ? 0 : k + 1;
-          const float e1 = SCALED ? drive[k] : fmaf(c.a, drive[k], c.f);
-          jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e0, e1);
-        }
-      }
+      for (int i = 0; i < ILP; ++i) jj_wrap(x[i], w[i]);
     }
-#pragma unroll
-    for (int i = 0; i < ILP; ++i) jj_wrap(x[i], w[i]);
     // Flush the FP32 partial sums at absolute 64-step boundaries, so that a
     // run split at any multiple of 64 steps reproduces the unsplit sums.
-    if (ACC && ((g + 1) & 15) == 0) {
+    if (ACC && ((ge + 1) & 15) == 0) {
 #pragma unroll
       for (int i = 0; i < ILP; ++i) {
         vs[i] += (double)acc[i];
