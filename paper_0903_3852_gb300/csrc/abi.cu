@@ -173,10 +173,9 @@ cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
 }
 
 sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp, int block,
-                      bool time_it, bool capturing = false, int32_t unit_cap = 0) {
+                      bool time_it, bool capturing = false) {
   JJLaunchArgs a = jj_args(c, r, ilp);
   const JJUnitList &L = c->units[paths_per_thread(ilp)];
-  if (unit_cap > 0 && a.unit_end > unit_cap) a.unit_end = unit_cap;
   if (time_it) SDE_CUDA_TRY(record(c->ev0, s, capturing));
   if (c->cfg.schedule == SDE_SCHED_PERSISTENT) {
     if (L.n_units > 0) {
@@ -200,10 +199,8 @@ sde_status jj_enqueue(sde_ctx *c, const sde_run_desc *r, cudaStream_t s, int ilp
   return SDE_OK;
 }
 
-constexpr int32_t kTunePaths = 786432;
-
-// Time each candidate launch shape on a short run over the leading units of
-// the work list and keep the fastest.  Uses scratch state, so the caller's
+// Time each candidate launch shape on a short run (the first few hundred to
+// 2048 steps) over the whole work list and keep the fastest.  Uses scratch state, so the caller's
 // buffers are untouched.
 sde_status jj_autotune(sde_ctx *c) {
   std::vector<std::pair<int, int>> cand;
@@ -257,7 +254,10 @@ sde_status jj_autotune(sde_ctx *c) {
     r.n_begin = 0;
     int64_t max_steps = 0;
     for (auto S : c->steps) max_steps = std::max(max_steps, S);
-    r.n_end = std::min<int64_t>(max_steps, 2048);
+    // every unit of the work list (the waves and the tail of the real run),
+    // for 256 to 2048 steps: about 2^31 path-steps per trial at most
+    const int64_t trial = std::min<int64_t>(2048, std::max<int64_t>(256, (1ll << 31) / np));
+    r.n_end = std::min<int64_t>(max_steps, trial);
     r.x_in_dev = x;
     r.v_in_dev = v;
     r.x_out_dev = x;
@@ -268,10 +268,7 @@ sde_status jj_autotune(sde_ctx *c) {
     for (auto &cd : cand) {
       float ms_min = 1e30f;
       for (int rep = 0; rep < 3 && st == SDE_OK; ++rep) {
-        // the first ~786k paths of the longest-first list (the same paths for
-        // every candidate): enough to fill the GPU many times over
-        st = jj_enqueue(c, &r, s, cd.second, cd.first, true, false,
-                        kTunePaths / (32 * paths_per_thread(cd.second)));
+        st = jj_enqueue(c, &r, s, cd.second, cd.first, true, false);
         if (st != SDE_OK) break;
         if ((e = cudaEventSynchronize(c->ev1)) != cudaSuccess) {
           fail(e, "autotune sync");

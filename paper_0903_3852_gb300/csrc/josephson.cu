@@ -180,12 +180,29 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
   // Blocks of 16 groups (64 steps) aligned to absolute step indices; the
   // FP32 partial sums are flushed after each block, outside the group loop,
   // so the FP64 adds run once per 64 steps.
+  // PIPE (four or more paths per thread): the Gaussians of group g + 1 are
+  // drawn while group g is stepped, in one basic block, so the integer Philox
+  // work interleaves with the FP32 steps (16 more live registers; with fewer
+  // paths per thread the lost occupancy costs more than the overlap gains).
+  constexpr bool PIPE = ILP >= 4;
+  float z[ILP][4];
+  if constexpr (PIPE) {
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) gauss4_tab(g0, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
+  }
   for (uint32_t gb = g0; gb <= g1; gb = (gb | 15u) + 1u) {
     const uint32_t ge = (gb | 15u) < g1 ? (gb | 15u) : g1;
     for (uint32_t g = gb; g <= ge; ++g) {
-      float z[ILP][4];
+      // PIPE: the Philox words of group g + 1 now, their Box-Muller
+      // transform into z once this group's steps have read it
+      uint4 rn[ILP];
 #pragma unroll
-      for (int i = 0; i < ILP; ++i) gauss4_tab(g, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
+      for (int i = 0; i < ILP; ++i) {
+        if constexpr (PIPE)
+          rn[i] = philox4x32_10(make_uint4(g + 1, pid[i], point, kTagJosephson), key);
+        else
+          gauss4_tab(g, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
+      }
       const int64_t base = (int64_t)g << 2;
       if (base >= n0 && base + 4 <= n1) {
         // full group: drive values at t_{4g} .. t_{4g+4}
@@ -222,7 +239,13 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
         }
       }
 #pragma unroll
-      for (int i = 0; i < ILP; ++i) jj_wrap(x[i], w[i]);
+      for (int i = 0; i < ILP; ++i) {
+        jj_wrap(x[i], w[i]);
+        if constexpr (PIPE) {
+          box_muller_tab(rn[i].x, rn[i].y, bm_tab, z[i][0], z[i][1]);
+          box_muller_tab(rn[i].z, rn[i].w, bm_tab, z[i][2], z[i][3]);
+        }
+      }
     }
     // Flush the FP32 partial sums at absolute 64-step boundaries, so that a
     // run split at any multiple of 64 steps reproduces the unsplit sums.
@@ -383,9 +406,10 @@ __global__ void __launch_bounds__(512, 2) jj_kernel_cap64(const JJLaunchArgs A) 
 
 // Packed-pair kernels (2 or 4 paths per thread) at the fewest registers that
 // hold them without spills: 72 for one pair (28 warps per SM in blocks of
-// 128), 88 for two (20 warps, each with two independent pairs in flight).
+// 128), 128 for two pairs with the noise of the next group in flight (16
+// warps, each with two independent pairs and the Philox work to overlap).
 template <int ILP, bool EM = false>
-__global__ void __maxnreg__(ILP == 2 ? 72 : 88) jj_kernel_packed(const JJLaunchArgs A) {
+__global__ void __maxnreg__(ILP == 2 ? 72 : 128) jj_kernel_packed(const JJLaunchArgs A) {
   jj_kernel_body<ILP, EM>(A);
 }
 
