@@ -468,7 +468,7 @@ def run_ours(args, rank, world, device):
     # summarised under profiles/ (null where the kernel changed since)
     traffic, traffic_src = None, None
     if args.workload in ("sweep", "plain", "fig2") and not args.euler:
-        traffic = 8.34 * n  # jj_kernel: 8.34 B per path (the initial state read once)
+        traffic = 8.23 * n  # jj_kernel: 8.23 B per path (the initial state read once)
         traffic_src = "profiles/jj_kernel_sweep_512pts_cap2000.md, scaled by paths"
     elif args.workload == "kuramoto-fig4":
         traffic = 16.9 * w["n_osc"] * w["replicas"]  # mean over the three launch kinds of a step

@@ -127,8 +127,8 @@ typedef struct sde_config {
   int32_t block_threads;    /* threads per block; 0 = autotune               */
   int32_t paths_per_thread; /* Josephson paths per thread: 1, 2 or 4 (2 and 4 advance
                                pairs of paths with packed FP32x2 instructions),
-                               or 11 / 12 for 1 / 2 with registers capped at
-                               64; 0 = autotune                                 */
+                               or 11 / 12 / 14 for 1 / 2 / 4 with fewer
+                               registers (64 / 64 / 96); 0 = autotune          */
   uint32_t flags;           /* SDE_FLAG_*                                     */
   int32_t cluster_ctas;     /* Kuramoto mean field: CTAs per replica (1, 2, 4 or
                                8, a thread-block cluster above 1); 0 = autotune

@@ -133,8 +133,9 @@ sde_status build_units(sde_ctx *c, int ilp) {
   return SDE_OK;
 }
 
-// Launch variants: 1, 2, 4 = paths per thread; 11, 12 = 1, 2 with registers
-// capped at 64.  The work list depends on the paths per thread only.
+// Launch variants: 1, 2, 4 = paths per thread; 11, 12, 14 = the same with
+// fewer registers (64, 64, 96).  The work list depends on the paths per
+// thread only.
 int paths_per_thread(int variant) { return variant % 10; }
 
 JJLaunchArgs jj_args(const sde_ctx *c, const sde_run_desc *r, int ilp) {
@@ -221,7 +222,7 @@ sde_status jj_autotune(sde_ctx *c) {
   else if (c->cfg.schedule == SDE_SCHED_PLAIN)
     il.push_back(1);  // the per-path kernel of Alg. 1: one thread per path
   else
-    il = {1, 2, 4, 12};
+    il = {2, 4, 12, 14};  // one path per thread never wins; it stays selectable
   // Euler-Maruyama kernels carry the variant code + 100
   const int scheme = (c->cfg.flags & SDE_FLAG_EULER) ? 100 : 0;
   for (int b : bl)
@@ -308,8 +309,9 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
                      cfg->block_threads % 32 == 0),
                 "block_threads must be 0 or a multiple of 32 in [32, 512]");
   SDE_CHECK_ARG(cfg->paths_per_thread == 0 || cfg->paths_per_thread == 1 || cfg->paths_per_thread == 2 ||
-                    cfg->paths_per_thread == 4 || cfg->paths_per_thread == 11 || cfg->paths_per_thread == 12,
-                "paths_per_thread must be 0, 1, 2, 4, 11 or 12");
+                    cfg->paths_per_thread == 4 || cfg->paths_per_thread == 11 || cfg->paths_per_thread == 12 ||
+                    cfg->paths_per_thread == 14,
+                "paths_per_thread must be 0, 1, 2, 4, 11, 12 or 14");
   c->n_points = cfg->n_points;
   c->P = cfg->steps_per_period;
   c->paths.resize(c->n_points);

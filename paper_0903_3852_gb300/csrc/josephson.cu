@@ -413,6 +413,14 @@ __global__ void __maxnreg__(ILP == 2 ? 72 : 128) jj_kernel_packed(const JJLaunch
   jj_kernel_body<ILP, EM>(A);
 }
 
+// Four paths per thread held to 96 registers (20 warps per SM in blocks of
+// 128): the autotuner weighs the extra warps against the compiler's freedom
+// to overlap.
+template <bool EM = false>
+__global__ void __maxnreg__(96) jj_kernel_packed4_cap96(const JJLaunchArgs A) {
+  jj_kernel_body<4, EM>(A);
+}
+
 __global__ void jj_prepare_kernel(const sde_jj_point *pts, int n_points, int P,
                                   const int64_t *steps, const int64_t *offsets,
                                   const int64_t *paths, JJConsts *out, float *drive) {
@@ -518,6 +526,7 @@ void *jj_kernel_ptr(int variant) {
     case 1: return (void *)jj_kernel<1>;
     case 2: return (void *)jj_kernel_packed<2>;
     case 4: return (void *)jj_kernel_packed<4>;
+    case 14: return (void *)jj_kernel_packed4_cap96<>;
     case 11: return (void *)jj_kernel_cap64<1>;
     case 12: return (void *)jj_kernel_cap64<2>;
     case 101: return (void *)jj_kernel<1, true>;
@@ -525,6 +534,7 @@ void *jj_kernel_ptr(int variant) {
     case 104: return (void *)jj_kernel_packed<4, true>;
     case 111: return (void *)jj_kernel_cap64<1, true>;
     case 112: return (void *)jj_kernel_cap64<2, true>;
+    case 114: return (void *)jj_kernel_packed4_cap96<true>;
   }
   return nullptr;
 }
@@ -540,14 +550,15 @@ cudaError_t jj_prepare(const sde_jj_point *points_dev, int n_points, int P, cons
   return cudaGetLastError();
 }
 
-// `ilp` encodes the variant: 1, 2, 4 = paths per thread; +10 = registers capped at 64
-// (1 and 2 only); +100 = Euler-Maruyama.
+// `ilp` encodes the variant: 1, 2, 4 = paths per thread; +10 = fewer registers
+// (64 for 1 and 2 paths per thread, 96 for 4); +100 = Euler-Maruyama.
 cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaStream_t s) {
   const size_t smem = jj_smem_bytes(a.P, block);
   switch (ilp) {
     case 1: jj_kernel<1><<<grid, block, smem, s>>>(a); break;
     case 2: jj_kernel_packed<2><<<grid, block, smem, s>>>(a); break;
     case 4: jj_kernel_packed<4><<<grid, block, smem, s>>>(a); break;
+    case 14: jj_kernel_packed4_cap96<><<<grid, block, smem, s>>>(a); break;
     case 11: jj_kernel_cap64<1><<<grid, block, smem, s>>>(a); break;
     case 12: jj_kernel_cap64<2><<<grid, block, smem, s>>>(a); break;
     // Euler-Maruyama variants: the code + 100
@@ -556,6 +567,7 @@ cudaError_t jj_launch(const JJLaunchArgs &a, int ilp, int block, int grid, cudaS
     case 104: jj_kernel_packed<4, true><<<grid, block, smem, s>>>(a); break;
     case 111: jj_kernel_cap64<1, true><<<grid, block, smem, s>>>(a); break;
     case 112: jj_kernel_cap64<2, true><<<grid, block, smem, s>>>(a); break;
+    case 114: jj_kernel_packed4_cap96<true><<<grid, block, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -576,7 +588,7 @@ int jj_max_blocks_per_sm(int ilp, int block, int P) {
 cudaError_t jj_configure() {
   static const cudaError_t status = [] {
     const int smem = (int)jj_smem_bytes(kWarpTableMaxP, kJJMaxBlock);
-    const int variants[] = {1, 2, 4, 11, 12, 101, 102, 104, 111, 112};
+    const int variants[] = {1, 2, 4, 11, 12, 14, 101, 102, 104, 111, 112, 114};
     for (int v : variants) {
       const cudaError_t e = cudaFuncSetAttribute(jj_kernel_ptr(v), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;

@@ -189,7 +189,7 @@ def test_launch_variants_are_bit_identical():
     steps = [1001, 2000, 7, 1500, 998]
     w = inputs.josephson_custom(pts, paths, steps, seed=4)
     ref = None
-    for ilp in (1, 11, 2, 12, 4):
+    for ilp in (1, 11, 2, 12, 4, 14):
         ens = _ens(pts, paths, steps, seed=4, paths_per_thread=ilp)
         out = jj_run(ens, w["x0"], w["v0"], 0, max(steps))
         got = [np.asarray(a) for a in out[:5]]  # per path: x, v, w, x mod 1, window sum
