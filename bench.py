@@ -33,6 +33,8 @@ from paper_0903_3852_gb300 import dist as sde_dist  # noqa: E402
 from paper_0903_3852_gb300 import inputs  # noqa: E402
 
 PAPER_FLOP_PER_STEP = 79  # Table 1 (Appendix): FLOP per SRK2 step of Eq. 1, weighted
+PAPER_FLOP_MEANFIELD = 66  # Fig. 5: operations per step of PROG3 (Eq. 3, mean field)
+PAPER_FLOP_PAIR = 6  # Fig. 5: 44 + 6N operations per step of PROG2, 6 per pair term
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -329,13 +331,13 @@ def run_ours(args, rank, world, device):
         elif model == sde.SDE_KURAMOTO_MEANFIELD:
             units = float(w["n_osc"] * w["replicas"] * S)
             metric = "oscillator-steps/sec"
-            flop_per_unit = 66  # Appendix: 66 FLOP per step of the mean-field program
+            flop_per_unit = PAPER_FLOP_MEANFIELD
             launches_per_step = 4
             flop_per_launch = flop_per_unit * units
         else:
             units = float(w["n_osc"] ** 2 * w["replicas"] * S)
             metric = "pair-terms/sec"
-            flop_per_unit = 6  # Appendix: 44 + 6N FLOP per oscillator-step, 6 per pair term
+            flop_per_unit = PAPER_FLOP_PAIR
             launches_per_step = 2 * S + S // w["sample_every"] + 4
             flop_per_launch = flop_per_unit * w["n_osc"] ** 2 * w["replicas"]  # one stage launch
         cfg = {"workload": "kuramoto_%s_N%d_R%d%s" % ("fig4_meanfield_grid" if fig4 else args.workload.split("-")[1],

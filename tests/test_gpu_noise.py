@@ -1,10 +1,11 @@
 """GPU parity of the noise generator: Philox4x32-10 draws bit-exact against the
-oracle (and the published known-answer vectors), Box-Muller Gaussians within
+oracle (and cuRAND's host-side Philox4_32_10 generator), Box-Muller Gaussians within
 FP32 rounding of the oracle's FP64 values from identical uniforms."""
 import numpy as np
 import pytest
 import torch
 
+import curand_ref
 import oracle
 from gpu_util import ensure_built
 from paper_0903_3852_gb300 import sde
@@ -23,19 +24,12 @@ def _to_dev(c):
     return torch.from_numpy(c.view(np.int32).copy()).cuda()
 
 
-def test_philox_known_answers_on_gpu(golden_dir):
+@pytest.mark.skipif(not curand_ref.available(), reason="libcurand not found")
+@pytest.mark.parametrize("seed,b0,n", curand_ref.CASES)
+def test_philox_matches_curand_on_gpu(seed, b0, n):
     ensure_built()
-    import os
-    rows = []
-    for line in open(os.path.join(golden_dir, "philox4x32_10_kat.txt")):
-        if line.strip() and not line.startswith("#"):
-            v = [int(t, 16) for t in line.split()]
-            rows.append(v)
-    for v in rows:
-        ctr = np.array([v[0:4]], dtype=np.uint32)
-        seed = v[4] | (v[5] << 32)
-        out = sde.philox4x32_10(_to_dev(ctr), seed).cpu().numpy().view(np.uint32)[0]
-        assert [int(x) for x in out] == v[6:10]
+    got = sde.philox4x32_10(_to_dev(curand_ref.counters(b0, n)), seed).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, curand_ref.blocks(seed, b0, n))
 
 
 @pytest.mark.parametrize("seed", [0, 1, 0x0123456789ABCDEF, 2 ** 64 - 1])
