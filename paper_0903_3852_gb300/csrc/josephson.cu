@@ -160,6 +160,36 @@ __host__ inline size_t jj_smem_bytes(int P, int block) {
   return sizeof(float) * (size_t)pp * (P <= kWarpTableMaxP ? 1 + block / 32 : 1);
 }
 
+// The Box-Muller transforms of the Philox blocks r[i] of ILP paths into their
+// four Gaussians z[i][0..3]: pairs of paths together on packed FP32 pairs
+// (the same roundings as one path at a time), so each packed pair of paths
+// gets its Gaussians already paired for jj_step2.
+template <int ILP>
+__device__ __forceinline__ void jj_transform(const uint4 (&r)[ILP], const float *bm_tab, float (&z)[ILP][4]) {
+  if constexpr (ILP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < ILP; i += 2) {
+      float2 Z0, Z1, Z2, Z3;
+      box_muller_tab2(r[i].x, r[i].y, r[i + 1].x, r[i + 1].y, bm_tab, Z0, Z1);
+      box_muller_tab2(r[i].z, r[i].w, r[i + 1].z, r[i + 1].w, bm_tab, Z2, Z3);
+      z[i][0] = Z0.x;
+      z[i + 1][0] = Z0.y;
+      z[i][1] = Z1.x;
+      z[i + 1][1] = Z1.y;
+      z[i][2] = Z2.x;
+      z[i + 1][2] = Z2.y;
+      z[i][3] = Z3.x;
+      z[i + 1][3] = Z3.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < ILP; ++i) {
+      box_muller_tab(r[i].x, r[i].y, bm_tab, z[i][0], z[i][1]);
+      box_muller_tab(r[i].z, r[i].w, bm_tab, z[i][2], z[i][3]);
+    }
+  }
+}
+
 // Advance ILP paths over the steps [n0, n1).  `k` is the drive-table index
 // of step n0 (n0 mod P) and is updated.
 // SCALED: `drive` holds a cos(2 pi k / P) + f for this point (a per-warp or
@@ -170,7 +200,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
                                            const float *__restrict__ drive, int P, int &k,
                                            int64_t n0, int64_t n1, const PhiloxKeys &key,
                                            const uint32_t (&pid)[ILP], uint32_t point,
-                                           const float2 *bm_tab) {
+                                           const float *bm_tab) {
   if (n0 >= n1) return;
   float acc[ILP];
 #pragma unroll
@@ -187,8 +217,10 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
   constexpr bool PIPE = ILP >= 4;
   float z[ILP][4];
   if constexpr (PIPE) {
+    uint4 r0[ILP];
 #pragma unroll
-    for (int i = 0; i < ILP; ++i) gauss4_tab(g0, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
+    for (int i = 0; i < ILP; ++i) r0[i] = philox4x32_10(make_uint4(g0, pid[i], point, kTagJosephson), key);
+    jj_transform<ILP>(r0, bm_tab, z);
   }
   for (uint32_t gb = g0; gb <= g1; gb = (gb | 15u) + 1u) {
     const uint32_t ge = (gb | 15u) < g1 ? (gb | 15u) : g1;
@@ -197,12 +229,9 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
       // transform into z once this group's steps have read it
       uint4 rn[ILP];
 #pragma unroll
-      for (int i = 0; i < ILP; ++i) {
-        if constexpr (PIPE)
-          rn[i] = philox4x32_10(make_uint4(g + 1, pid[i], point, kTagJosephson), key);
-        else
-          gauss4_tab(g, pid[i], point, kTagJosephson, key, bm_tab, z[i]);
-      }
+      for (int i = 0; i < ILP; ++i)
+        rn[i] = philox4x32_10(make_uint4(PIPE ? g + 1 : g, pid[i], point, kTagJosephson), key);
+      if constexpr (!PIPE) jj_transform<ILP>(rn, bm_tab, z);
       const int64_t base = (int64_t)g << 2;
       if (base >= n0 && base + 4 <= n1) {
         // full group: drive values at t_{4g} .. t_{4g+4}
@@ -239,13 +268,8 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
         }
       }
 #pragma unroll
-      for (int i = 0; i < ILP; ++i) {
-        jj_wrap(x[i], w[i]);
-        if constexpr (PIPE) {
-          box_muller_tab(rn[i].x, rn[i].y, bm_tab, z[i][0], z[i][1]);
-          box_muller_tab(rn[i].z, rn[i].w, bm_tab, z[i][2], z[i][3]);
-        }
-      }
+      for (int i = 0; i < ILP; ++i) jj_wrap(x[i], w[i]);
+      if constexpr (PIPE) jj_transform<ILP>(rn, bm_tab, z);
     }
     // Flush the FP32 partial sums at absolute 64-step boundaries, so that a
     // run split at any multiple of 64 steps reproduces the unsplit sums.
@@ -271,7 +295,7 @@ __device__ __forceinline__ double warp_sum(double a) {
 
 template <int ILP, bool EM>
 __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, float *wtab,
-                                        const float2 *bm_tab, int lane) {
+                                        const float *bm_tab, int lane) {
   const JJUnit un = A.units[u];
   const JJConsts c = A.consts[un.point];
   const PhiloxKeys &key = A.keys;
@@ -366,7 +390,7 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
   // drive table cos(2 pi k / P), k = 0 .. P + 3 (four entries of padding
   // repeat the start of the period), 16-byte aligned
   extern __shared__ float4 drive_s4[];
-  __shared__ float2 bm_tab[kBmTable];  // Box-Muller angle table
+  __shared__ float bm_tab[2 * kBmTable];  // Box-Muller angle table
   float *drive_s = reinterpret_cast<float *>(drive_s4);
   for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x) drive_s[i] = A.drive[i % A.P];
   fill_bm_table(bm_tab);
@@ -506,7 +530,7 @@ __global__ void box_muller_fill_kernel(const uint4 *ctr, uint2 key, float4 *z, i
 // library's default transform, 1 the Josephson kernels' (table angle,
 // hardware logarithm).
 __global__ void box_muller_words_kernel(const uint2 *w, int64_t n, int variant, float2 *z) {
-  __shared__ float2 tab[kBmTable];
+  __shared__ float tab[2 * kBmTable];
   fill_bm_table(tab);
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -669,7 +693,7 @@ struct NoallocArgs {
 // unit decomposition as the plain schedule with one path per thread.
 __global__ void __launch_bounds__(256) jj_noalloc_kernel(const NoallocArgs A) {
   extern __shared__ float4 drive_s4[];
-  __shared__ float2 bm_tab[kBmTable];
+  __shared__ float bm_tab[2 * kBmTable];
   float *drive_s = reinterpret_cast<float *>(drive_s4);
   const double dt = 2.0 * 3.14159265358979323846 / (A.p.omega * (double)A.P);
   for (int i = threadIdx.x; i < A.P + 4; i += blockDim.x)

@@ -143,34 +143,61 @@ __device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uin
 //    u0 -> 1 (radius -> 0); the radius error stays below ~5e-4 everywhere
 //    (the bound the tests check on all 2^24 values of u0).  A slightly
 //    positive log of a u0 just below 1 is clamped to a zero radius.
-// tab[q] = (cos, sin)(2 pi q / 1024), q = 0 .. 1023, filled by fill_bm_table
-// (shared memory of the calling kernel, 8 KB).
+// tab[q] = cos(2 pi q / 1024) and tab[kBmTable + q] = sin(2 pi q / 1024),
+// q = 0 .. 1023, filled by fill_bm_table (shared memory of the calling
+// kernel, 8 KB); separate cos and sin arrays, so that two lookups can land in
+// the two halves of a packed FP32 pair.
 constexpr int kBmTable = 1024;
 
-__device__ __forceinline__ void fill_bm_table(float2 *tab) {
+__device__ __forceinline__ void fill_bm_table(float *tab) {
   for (int q = threadIdx.x; q < kBmTable; q += blockDim.x) {
     float sn, cs;
     sincospif((float)q * 0.001953125f, &sn, &cs);  // q / 512
-    tab[q] = make_float2(cs, sn);
+    tab[q] = cs;
+    tab[kBmTable + q] = sn;
   }
 }
 
-__device__ __forceinline__ void box_muller_tab(uint32_t w0, uint32_t w1, const float2 *tab, float &z0,
+__device__ __forceinline__ void box_muller_tab(uint32_t w0, uint32_t w1, const float *tab, float &z0,
                                                float &z1) {
   const float u0 = fmaf((float)(w0 >> 8), 5.9604644775390625e-8f, 5.9604644775390625e-8f);  // exact
   float l2;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(u0));
   const float rho = radius(fmaxf(-1.38629436111989061883f * l2, 0.0f));  // -2 ln 2 log2(u0)
-  const float2 t = tab[w1 >> 22];
+  const float2 t = make_float2(tab[w1 >> 22], tab[kBmTable + (w1 >> 22)]);
   const float b = fmaf((float)((w1 >> 8) & 0x3FFFu), 3.7450702829239308e-7f, 3.7450702829239308e-7f);  // 2 pi 2^-24
   const float cb = fmaf(-0.5f * b, b, 1.0f);
   z0 = rho * fmaf(t.x, cb, -t.y * b);
   z1 = rho * fmaf(t.y, cb, t.x * b);
 }
 
+// box_muller_tab for two word pairs at once (the same words of two paths) on
+// packed FP32 pairs: Z0 = (z0 of A, z0 of B), Z1 = (z1 of A, z1 of B), the
+// same roundings as box_muller_tab element by element.
+__device__ __forceinline__ void box_muller_tab2(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1,
+                                                const float *tab, float2 &Z0, float2 &Z1) {
+  const float2 q = make_float2(5.9604644775390625e-8f, 5.9604644775390625e-8f);  // 2^-24
+  const float2 u0 = __ffma2_rn(make_float2((float)(a0 >> 8), (float)(b0 >> 8)), q, q);
+  float la, lb;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(la) : "f"(u0.x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lb) : "f"(u0.y));
+  const float2 L = __fmul2_rn(make_float2(-1.38629436111989061883f, -1.38629436111989061883f),
+                              make_float2(la, lb));
+  const float2 rho = make_float2(radius(fmaxf(L.x, 0.0f)), radius(fmaxf(L.y, 0.0f)));
+  const float2 c = make_float2(3.7450702829239308e-7f, 3.7450702829239308e-7f);  // 2 pi 2^-24
+  const float2 b =
+      __ffma2_rn(make_float2((float)((a1 >> 8) & 0x3FFFu), (float)((b1 >> 8) & 0x3FFFu)), c, c);
+  const float2 cb = __ffma2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), b), b, make_float2(1.0f, 1.0f));
+  const float2 tx = make_float2(tab[a1 >> 22], tab[b1 >> 22]);
+  const float2 ty = make_float2(tab[kBmTable + (a1 >> 22)], tab[kBmTable + (b1 >> 22)]);
+  const float2 nb = make_float2(-b.x, -b.y);
+  Z0 = __fmul2_rn(rho, __ffma2_rn(tx, cb, __fmul2_rn(ty, nb)));
+  Z1 = __fmul2_rn(rho, __ffma2_rn(ty, cb, __fmul2_rn(tx, b)));
+}
+
 // gauss4 with round keys and the Box-Muller angle table.
 __device__ __forceinline__ void gauss4_tab(uint32_t g, uint32_t c1, uint32_t c2, uint32_t tag,
-                                           const PhiloxKeys &K, const float2 *tab, float (&z)[4]) {
+                                           const PhiloxKeys &K, const float *tab, float (&z)[4]) {
   const uint4 r = philox4x32_10(make_uint4(g, c1, c2, tag), K);
   box_muller_tab(r.x, r.y, tab, z[0], z[1]);
   box_muller_tab(r.z, r.w, tab, z[2], z[3]);
