@@ -180,6 +180,44 @@ def test_small_sweep_pathwise_and_rows():
             off += npk
 
 
+@pytest.mark.parametrize("period", [1, 3, 7, 1020, 1021, 4096])
+def test_drive_period_edge_values(period):
+    # P = 1: a constant drive; P not a multiple of 4: the drive term read entry
+    # by entry; P > 1020: no per-warp prescaled table (the shared table and the
+    # drive formed in the step); P = 4096: the largest period accepted.  A
+    # deterministic point (D = 0) rides along; ragged path counts, a window
+    # that does not start on a 4-step group
+    ensure_built()
+    # the usual dt = 2 pi / (4.9 x 200) at every period, and a drive and bias
+    # well below the critical tilt 2 pi: every path stays locked in a well,
+    # where rounding errors decay (a running path's phase is neutral and would
+    # accumulate them past the bar at the slow or constant drives of P = 4096
+    # and P = 1)
+    omega = 4.9 * 200 / period
+    pts = [dict(gamma=3.0, a=1.0, omega=omega, f=0.1, D=1e-3), dict(gamma=3.0, a=1.0, omega=omega, f=0.3, D=0.0)]
+    paths = [97, 33]
+    steps = 601
+    w = inputs.josephson_custom(pts, paths, [steps, steps], seed=6)
+    ref = None
+    for ilp in (1, 4):
+        ens = sde.Ensemble.josephson(pts, paths, [steps, steps], 6, steps_per_period=period, paths_per_thread=ilp)
+        xg, vg, wg, fg, sg, obs = jj_run(ens, w["x0"], w["v0"], 0, steps)
+        off = 0
+        for k, (pt, npk) in enumerate(zip(pts, paths)):
+            sl = slice(off, off + npk)
+            xo, vo, so = oracle.jj_run(w["x0"][sl], w["v0"][sl], oracle.jj_params(**pt), period, 0, steps, steps,
+                                       6, k, 0, None)
+            assert mixed_rel(xg[sl], xo).max() <= 1e-5 and mixed_rel(vg[sl], vo).max() <= 1e-5, (period, k)
+            assert np.allclose(sg[sl], so, rtol=1e-5, atol=1e-4 * (steps // 2))
+            off += npk
+        got = [np.asarray(a) for a in (xg, vg, wg, sg)]
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), period
+
+
 def test_launch_variants_are_bit_identical():
     # one path per thread (scalar FP32) and pairs of paths on packed FP32x2
     # instructions (2 and 4 per thread, capped registers) perform the same
