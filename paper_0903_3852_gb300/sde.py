@@ -131,7 +131,7 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError("libsde_gb300.so is not built (%s); run "
-                               "python -c 'import __graft_entry__ as g; g.build()'" % LIB_PATH)
+                               "python -m paper_0903_3852_gb300.build" % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         for name, res, args in SIGNATURES:
             fn = getattr(L, name)
