@@ -685,18 +685,23 @@ __global__ void __launch_bounds__(kMfgThreads, MODE == 3 ? 4 : (MODE == 2 ? 8 : 
 
 // ---- pairwise form (Alg. 3) --------------------------------------------
 
-// sin(2 pi d) for a phase difference d in turns, |d| < 2^22: d is first
-// reduced to [-1/2, 1/2] by subtracting rint(d) (computed by adding and
-// subtracting 1.5 * 2^23 on the FMA pipe), so that the one special-function
-// instruction sees an argument in [-pi, pi].
-__device__ __forceinline__ float sin2pi_diff(float d) {
-  const float r = d - ((d + 12582912.0f) - 12582912.0f);
-  return __sinf(6.28318530717958647692f * r);
-}
-
 constexpr int kPairThreads = 128;
-constexpr int kPairPerThread = 2;  // receivers per thread
+constexpr int kPairPerThread = 2;  // receivers per thread: one packed FP32 pair
 constexpr int kPairTile = kPairThreads * kPairPerThread;
+
+// acc += sin(2 pi (t - ti)) for the thread's two receivers ti = (ti0, ti1),
+// phases in turns, on packed FP32 pairs: the difference d is reduced to
+// [-1/2, 1/2] by subtracting rint(d) (adding and subtracting 1.5 * 2^23 on
+// the FMA pipe, |d| < 2^22), so that the one special-function sin per
+// receiver sees an argument in [-pi, pi].  tt = (t, t), nti = (-ti0, -ti1).
+__device__ __forceinline__ void pair_terms2(float2 tt, float2 nti, float2 &acc) {
+  const float2 d = __fadd2_rn(tt, nti);
+  const float2 m = __fadd2_rn(__fadd2_rn(d, make_float2(12582912.0f, 12582912.0f)),
+                              make_float2(-12582912.0f, -12582912.0f));
+  const float2 r = __ffma2_rn(m, make_float2(-1.0f, -1.0f), d);
+  const float2 a = __fmul2_rn(r, make_float2(6.28318530717958647692f, 6.28318530717958647692f));
+  acc = __fadd2_rn(acc, make_float2(__sinf(a.x), __sinf(a.y)));
+}
 
 // One SRK2 stage: receivers i of one replica in this CTA, all sources j
 // streamed through shared memory in tiles.  STAGE 0 (predictor) reads the
@@ -706,7 +711,7 @@ constexpr int kPairTile = kPairThreads * kPairPerThread;
 // AdvanceSystem kernel of the Euler-Maruyama scheme.
 template <int STAGE>
 __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPairArgs A) {
-  __shared__ float src_s[kPairTile];
+  __shared__ float2 src_s[kPairTile];  // each source phase twice: (t, t)
   const int rep = blockIdx.y;
   const int64_t N = A.N;
   const int64_t base = (int64_t)rep * N;
@@ -719,30 +724,30 @@ __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPair
     ti[k] = idx[k] < N ? (float)(int32_t)src[base + idx[k]] * 2.3283064365386963e-10f : 0.0f;
     acc[k] = 0.0f;
   }
+  static_assert(kPairPerThread == 2, "the receivers of a thread form one packed pair");
+  const float2 nti = make_float2(-ti[0], -ti[1]);
+  float2 acc2 = make_float2(0.0f, 0.0f);
   for (int64_t j0 = 0; j0 < N; j0 += kPairTile) {
     const int cnt = (N - j0) < kPairTile ? (int)(N - j0) : kPairTile;
 #pragma unroll
     for (int k = 0; k < kPairPerThread; ++k) {
       const int jj = threadIdx.x + k * kPairThreads;
-      if (jj < cnt) src_s[jj] = (float)(int32_t)src[base + j0 + jj] * 2.3283064365386963e-10f;
+      if (jj < cnt) {
+        const float t = (float)(int32_t)src[base + j0 + jj] * 2.3283064365386963e-10f;
+        src_s[jj] = make_float2(t, t);
+      }
     }
     __syncthreads();
     if (cnt == kPairTile) {
 #pragma unroll 8
-      for (int jj = 0; jj < kPairTile; ++jj) {
-        const float tj = src_s[jj];
-#pragma unroll
-        for (int k = 0; k < kPairPerThread; ++k) acc[k] += sin2pi_diff(tj - ti[k]);
-      }
+      for (int jj = 0; jj < kPairTile; ++jj) pair_terms2(src_s[jj], nti, acc2);
     } else {
-      for (int jj = 0; jj < cnt; ++jj) {
-        const float tj = src_s[jj];
-#pragma unroll
-        for (int k = 0; k < kPairPerThread; ++k) acc[k] += sin2pi_diff(tj - ti[k]);
-      }
+      for (int jj = 0; jj < cnt; ++jj) pair_terms2(src_s[jj], nti, acc2);
     }
     __syncthreads();
   }
+  acc[0] = acc2.x;
+  acc[1] = acc2.y;
   if (STAGE == 2) {
 #pragma unroll
     for (int k = 0; k < kPairPerThread; ++k)
