@@ -598,46 +598,64 @@ __global__ void __launch_bounds__(kMfgThreads, MODE == 3 ? 4 : (MODE == 2 ? 8 : 
         a1[u] = y_r[ii];
       }
     }
+    // oscillators u and u + 1 together: their sin/cos polynomials on packed
+    // FP32 pairs (sincos_turns2), the rest per oscillator
+    static_assert(kMfgIlp % 2 == 0, "oscillators are taken in pairs");
 #pragma unroll
-    for (int u = 0; u < kMfgIlp; ++u) {
-      const uint32_t i = i0 + u * kMfgThreads;
-      float sn, cs;
+    for (int u = 0; u < kMfgIlp; u += 2) {
+      float2 sn, cs;
       if (MODE == 2) {
-        sincos_turns(t0[u], sn, cs);
+        sincos_turns2(t0[u], t0[u + 1], sn, cs);
       } else if (kPred) {
-        float s0, c0;
-        sincos_turns(t0[u], s0, c0);
-        const float g1 = c0 * S - s0 * C;
-        float psi = a2[u];
-        if (kGen) {
-          float z[4];
-          gauss4((uint32_t)(A.n >> 2), i, (uint32_t)rep, kTagKuramoto, A.keys, z);
-          psi = pick4(z, j);
-          if (ok[u]) {
+        float2 s0, c0;
+        sincos_turns2(t0[u], t0[u + 1], s0, c0);
+        uint32_t tp[2];
 #pragma unroll
-            for (int k = 1; k < 4; ++k)
-              if (k > j) psi_out[(int64_t)(k - 1) * NR + i] = z[k];
+        for (int e = 0; e < 2; ++e) {
+          const int v = u + e;
+          const uint32_t i = i0 + v * kMfgThreads;
+          const float g1 = (e ? c0.y : c0.x) * S - (e ? s0.y : s0.x) * C;
+          float psi = a2[v];
+          if (kGen) {
+            float z[4];
+            gauss4((uint32_t)(A.n >> 2), i, (uint32_t)rep, kTagKuramoto, A.keys, z);
+            psi = pick4(z, j);
+            if (ok[v]) {
+#pragma unroll
+              for (int k = 1; k < 4; ++k)
+                if (k > j) psi_out[(int64_t)(k - 1) * NR + i] = z[k];
+            }
+          }
+          const float wdt = a1[v] * A.wscale;
+          const float d1 = fmaf(A.sc, psi, fmaf(A.kc, g1, wdt));
+          tp[e] = t0[v] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+          if (ok[v]) {
+            tt_r[i] = tp[e];
+            y_r[i] = fmaf(A.sc, psi, fmaf(A.kh, g1, wdt));
           }
         }
-        const float wdt = a1[u] * A.wscale;
-        const float d1 = fmaf(A.sc, psi, fmaf(A.kc, g1, wdt));
-        const uint32_t tp = t0[u] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
-        if (ok[u]) {
-          tt_r[i] = tp;
-          y_r[i] = fmaf(A.sc, psi, fmaf(A.kh, g1, wdt));
-        }
-        sincos_turns(tp, sn, cs);
+        sincos_turns2(tp[0], tp[1], sn, cs);
       } else {
-        float s2, c2;
-        sincos_turns(tt[u], s2, c2);
-        const float g2 = c2 * S - s2 * C;
-        const uint32_t t1 = t0[u] + (uint32_t)__float2int_rn(fmaf(A.kh, g2, a1[u]) * 4294967296.0f);
-        if (ok[u]) th_r[i] = t1;
-        sincos_turns(t1, sn, cs);
+        float2 s2, c2;
+        sincos_turns2(tt[u], tt[u + 1], s2, c2);
+        uint32_t t1[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int v = u + e;
+          const uint32_t i = i0 + v * kMfgThreads;
+          const float g2 = (e ? c2.y : c2.x) * S - (e ? s2.y : s2.x) * C;
+          t1[e] = t0[v] + (uint32_t)__float2int_rn(fmaf(A.kh, g2, a1[v]) * 4294967296.0f);
+          if (ok[v]) th_r[i] = t1[e];
+        }
+        sincos_turns2(t1[0], t1[1], sn, cs);
       }
       if (ok[u]) {
-        ps += sn;
-        pc += cs;
+        ps += sn.x;
+        pc += cs.x;
+      }
+      if (ok[u + 1]) {
+        ps += sn.y;
+        pc += cs.y;
       }
     }
   }

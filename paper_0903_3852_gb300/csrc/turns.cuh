@@ -30,4 +30,26 @@ __device__ __forceinline__ void sincos_turns(uint32_t th, float &sn, float &cs) 
   cs = ((q + 1u) & 2u) ? -cc : cc;
 }
 
+// sincos_turns of two phases at once, the polynomials on packed FP32 pairs
+// (the same roundings as sincos_turns element by element).
+__device__ __forceinline__ void sincos_turns2(uint32_t ta, uint32_t tb, float2 &sn, float2 &cs) {
+  const uint32_t qa = (ta + 0x20000000u) >> 30, qb = (tb + 0x20000000u) >> 30;
+  const float2 x = __fmul2_rn(make_float2((float)(int32_t)(ta - (qa << 30)), (float)(int32_t)(tb - (qb << 30))),
+                              make_float2(1.46291807926715968e-9f, 1.46291807926715968e-9f));
+  const float2 x2 = __fmul2_rn(x, x);
+  const float2 ps = __ffma2_rn(__ffma2_rn(x2, make_float2(-1.956071210e-4f, -1.956071210e-4f),
+                                          make_float2(8.332642727e-3f, 8.332642727e-3f)),
+                               x2, make_float2(-1.666666716e-1f, -1.666666716e-1f));
+  const float2 s = __ffma2_rn(__fmul2_rn(x, x2), ps, x);
+  float2 pc = __ffma2_rn(x2, make_float2(2.456674520e-5f, 2.456674520e-5f),
+                         make_float2(-1.388842822e-3f, -1.388842822e-3f));
+  pc = __ffma2_rn(x2, pc, make_float2(4.166666791e-2f, 4.166666791e-2f));
+  pc = __ffma2_rn(x2, pc, make_float2(-0.5f, -0.5f));
+  const float2 c = __ffma2_rn(x2, pc, make_float2(1.0f, 1.0f));
+  const float ssa = (qa & 1u) ? c.x : s.x, cca = (qa & 1u) ? s.x : c.x;
+  const float ssb = (qb & 1u) ? c.y : s.y, ccb = (qb & 1u) ? s.y : c.y;
+  sn = make_float2((qa & 2u) ? -ssa : ssa, (qb & 2u) ? -ssb : ssb);
+  cs = make_float2(((qa + 1u) & 2u) ? -cca : cca, ((qb + 1u) & 2u) ? -ccb : ccb);
+}
+
 }  // namespace sde
