@@ -132,9 +132,9 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
       if (s < s0 || s >= s1) continue;
       float sn[OPT], cs[OPT];
       int S = 0, C = 0;
+      sincos_turns_n<OPT>(th, sn, cs);
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
-        sincos_turns(th[k], sn[k], cs[k]);
         if (!valid[k]) sn[k] = cs[k] = 0.0f;
         S += quant(sn[k]);
         C += quant(cs[k]);
@@ -151,11 +151,16 @@ __global__ void __launch_bounds__(OPT <= 2 ? 1024 : 512, 1) kur_meanfield_kernel
       if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
       float g1[OPT], sn2[OPT], cs2[OPT];
       int S2 = 0, C2 = 0;
+      uint32_t tp[OPT];
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
-        sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
+        tp[k] = th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+      }
+      sincos_turns_n<OPT>(tp, sn2, cs2);
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
         S2 += quant(sn2[k]);
         C2 += quant(cs2[k]);
@@ -260,9 +265,9 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
       if (s < s0 || s >= s1) continue;
       float sn[OPT], cs_[OPT];
       int S = 0, C = 0;
+      sincos_turns_n<OPT>(th, sn, cs_);
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
-        sincos_turns(th[k], sn[k], cs_[k]);
         if (!valid[k]) sn[k] = cs_[k] = 0.0f;
         S += quant(sn[k]);
         C += quant(cs_[k]);
@@ -278,11 +283,16 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_cluster_kernel(const Kur
       if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
       float g1[OPT], sn2[OPT], cs2[OPT];
       int S2 = 0, C2 = 0;
+      uint32_t tp[OPT];
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
-        sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
+        tp[k] = th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+      }
+      sincos_turns_n<OPT>(tp, sn2, cs2);
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
         S2 += quant(sn2[k]);
         C2 += quant(cs2[k]);
@@ -455,9 +465,9 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
       if (s < s0 || s >= s1 || failed) continue;
       float sn[OPT], cs_[OPT];
       int S = 0, C = 0;
+      sincos_turns_n<OPT>(th, sn, cs_);
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
-        sincos_turns(th[k], sn[k], cs_[k]);
         if (!valid[k]) sn[k] = cs_[k] = 0.0f;
         S += quant(sn[k]);
         C += quant(cs_[k]);
@@ -473,11 +483,16 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
       if (A.M > 0 && ++sample_ctr == A.M) sample_ctr = 0;
       float g1[OPT], sn2[OPT], cs2[OPT];
       int S2 = 0, C2 = 0;
+      uint32_t tp[OPT];
 #pragma unroll
       for (int k = 0; k < OPT; ++k) {
         g1[k] = cs_[k] * sc.x - sn[k] * sc.y;
         const float d1 = fmaf(A.sc, z[k][s], fmaf(A.kc, g1[k], wdt[k]));
-        sincos_turns(th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f), sn2[k], cs2[k]);
+        tp[k] = th[k] + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+      }
+      sincos_turns_n<OPT>(tp, sn2, cs2);
+#pragma unroll
+      for (int k = 0; k < OPT; ++k) {
         if (!valid[k]) sn2[k] = cs2[k] = 0.0f;
         S2 += quant(sn2[k]);
         C2 += quant(cs2[k]);

@@ -52,4 +52,20 @@ __device__ __forceinline__ void sincos_turns2(uint32_t ta, uint32_t tb, float2 &
   cs = make_float2(((qa + 1u) & 2u) ? -cca : cca, ((qb + 1u) & 2u) ? -ccb : ccb);
 }
 
+// sincos_turns of n phases, two at a time on packed pairs (one alone if n is
+// odd).
+template <int N>
+__device__ __forceinline__ void sincos_turns_n(const uint32_t (&th)[N], float (&sn)[N], float (&cs)[N]) {
+#pragma unroll
+  for (int k = 0; k + 1 < N; k += 2) {
+    float2 s, c;
+    sincos_turns2(th[k], th[k + 1], s, c);
+    sn[k] = s.x;
+    sn[k + 1] = s.y;
+    cs[k] = c.x;
+    cs[k + 1] = c.y;
+  }
+  if (N & 1) sincos_turns(th[N - 1], sn[N - 1], cs[N - 1]);
+}
+
 }  // namespace sde
