@@ -147,6 +147,21 @@ def sweep_workload(rank, args=None):
     return w
 
 
+def josephson_workload_name(args, w):
+    name = {"sweep": "josephson_sweep_%dpts" % len(w["points"]), "plain": "josephson_plain_1024",
+            "fig2": "josephson_fig2_524288paths_2e5steps"}[args.workload]
+    if args.steps_cap:
+        name += "_cap%d" % args.steps_cap
+    if args.euler:
+        name += "_euler"
+    return name
+
+
+def josephson_sizes(w):
+    return {"points": len(w["points"]), "total_paths": int(w["paths"].sum()),
+            "path_steps": float((w["paths"] * w["steps"]).sum()), "steps_per_period": w["steps_per_period"]}
+
+
 def plain_workload(rank):
     w = inputs.josephson_plain()
     w["seed"] = sde_dist.rank_seed(w["seed"], rank)
@@ -224,17 +239,10 @@ def run_ours(args, rank, world, device):
         launches_kernel = 1  # the timed region brackets the per-step launches as one
         metric = "path-steps/sec"
         flop_per_unit = PAPER_FLOP_PER_STEP
-        name = {"sweep": "josephson_sweep_%dpts" % len(w["points"]), "plain": "josephson_plain_1024",
-                "fig2": "josephson_fig2_524288paths_2e5steps"}[args.workload]
-        if args.steps_cap:
-            name += "_cap%d" % args.steps_cap
-        if args.euler:
-            name += "_euler"
+        name = josephson_workload_name(args, w)
         if args.workload != "plain" and sched == sde.SDE_SCHED_PLAIN:
             name += "_plain_per_point"
-        cfg = {"workload": name,
-               "points": len(w["points"]), "total_paths": n, "path_steps": units,
-               "steps_per_period": w["steps_per_period"],
+        cfg = {"workload": name, **josephson_sizes(w),
                "schedule": "persistent+graph" if sched == sde.SDE_SCHED_PERSISTENT else "plain per point",
                "tuning": dict(zip(("block_threads", "paths_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write); state 9 MB, compute-bound"}
@@ -479,7 +487,7 @@ def run_ours(args, rank, world, device):
         traffic = 146.2e6  # tc_gemm_bf16_kernel: K (134 MB) once + operands and output
         traffic_src = "profiles/tc_gemm_bf16_kernel_N8192_R256.md"
     elif args.workload == "kuramoto-meanfield":
-        traffic = 2.16e6  # phases and omega read once per run; results stay in L2
+        traffic = 2.43e6  # phases and omega read once per run; results stay in L2
         traffic_src = "profiles/kur_meanfield_cluster_kernel_N4096_R64.md"
     elif args.workload == "kuramoto-pairwise" and not args.euler:
         traffic = 2.12e6
@@ -695,6 +703,16 @@ def cpu_baseline(args, budget_s=20.0):
             "sample": "replica 0, %d steps" % S}
 
 
+def reference_config(args, sample):
+    """The reference arm's config: the workload as the GPU arm names and sizes
+    it (Josephson workloads), plus the bounded sample the oracle ran."""
+    if args.workload in ("sweep", "plain", "fig2"):
+        w = {"sweep": lambda: sweep_workload(0, args), "plain": lambda: plain_workload(0),
+             "fig2": lambda: fig2_workload(0)}[args.workload]()
+        return {"workload": josephson_workload_name(args, w), **josephson_sizes(w), "sample": sample}
+    return {"workload": args.workload, "sample": sample}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, K bounded steps."""
     rank = int(os.environ.get("RANK", "0"))
@@ -728,7 +746,7 @@ def run_reference(args):
     res = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; inputs.py)",
-           "config": {"workload": args.workload, "sample": last["sample"]},
+           "config": reference_config(args, last["sample"]),
            "cpu_baseline": {"value": v, "unit": unit, "cores": last["cores"], "kind": "oracle",
                             "sample": last["sample"], "single_core": one},
            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
