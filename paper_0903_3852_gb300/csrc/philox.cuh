@@ -108,27 +108,6 @@ __device__ __forceinline__ void gauss4(uint32_t g, uint32_t c1, uint32_t c2, uin
   box_muller(r.z, r.w, z[2], z[3]);
 }
 
-// The one Gaussian of step n of a stream, identical to element n & 3 of
-// gauss4 for the block n / 4 (only the Box-Muller pair that holds it is
-// evaluated).
-__device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uint32_t tag, uint2 key) {
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 2), c1, c2, tag), key);
-  const bool hi = (n & 2) != 0;
-  float z0, z1;
-  box_muller(hi ? r.z : r.x, hi ? r.w : r.y, z0, z1);
-  return (n & 1) ? z1 : z0;
-}
-
-// gauss1 with precomputed round keys.
-__device__ __forceinline__ float gauss1(int64_t n, uint32_t c1, uint32_t c2, uint32_t tag,
-                                        const PhiloxKeys &K) {
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)(n >> 2), c1, c2, tag), K);
-  const bool hi = (n & 2) != 0;
-  float z0, z1;
-  box_muller(hi ? r.z : r.x, hi ? r.w : r.y, z0, z1);
-  return (n & 1) ? z1 : z0;
-}
-
 // Box-Muller of the Josephson kernels, two shortcuts against box_muller:
 //  * the angle's sine and cosine from a table: the angle 2 pi u1,
 //    u1 = (j + 1) 2^-24 with j = w1 >> 8, is split into the table angle
@@ -193,14 +172,6 @@ __device__ __forceinline__ void box_muller_tab2(uint32_t a0, uint32_t a1, uint32
   const float2 nb = make_float2(-b.x, -b.y);
   Z0 = __fmul2_rn(rho, __ffma2_rn(tx, cb, __fmul2_rn(ty, nb)));
   Z1 = __fmul2_rn(rho, __ffma2_rn(ty, cb, __fmul2_rn(tx, b)));
-}
-
-// gauss4 with round keys and the Box-Muller angle table.
-__device__ __forceinline__ void gauss4_tab(uint32_t g, uint32_t c1, uint32_t c2, uint32_t tag,
-                                           const PhiloxKeys &K, const float *tab, float (&z)[4]) {
-  const uint4 r = philox4x32_10(make_uint4(g, c1, c2, tag), K);
-  box_muller_tab(r.x, r.y, tab, z[0], z[1]);
-  box_muller_tab(r.z, r.w, tab, z[2], z[3]);
 }
 
 // Element k (0..3) of a 4-vector without dynamic register indexing.
