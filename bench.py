@@ -481,7 +481,7 @@ def run_ours(args, rank, world, device):
         traffic = 8.23 * n  # jj_kernel: 8.23 B per path (the initial state read once)
         traffic_src = "profiles/jj_kernel_sweep_512pts_cap2000.md, scaled by paths"
     elif args.workload == "kuramoto-fig4":
-        traffic = 16.9 * w["n_osc"] * w["replicas"]  # mean over the three launch kinds of a step
+        traffic = 16.6 * w["n_osc"] * w["replicas"]  # mean over the launches of 4 steps
         traffic_src = "profiles/kur_mfg_kernel_fig4_N16777216.md"
     elif args.workload == "kuramoto-general" and not args.fused:
         traffic = 146.2e6  # tc_gemm_bf16_kernel: K (134 MB) once + operands and output
@@ -490,7 +490,7 @@ def run_ours(args, rank, world, device):
         traffic = 2.43e6  # phases and omega read once per run; results stay in L2
         traffic_src = "profiles/kur_meanfield_cluster_kernel_N4096_R64.md"
     elif args.workload == "kuramoto-pairwise" and not args.euler:
-        traffic = 2.12e6
+        traffic = 2.11e6
         traffic_src = "profiles/kur_pairwise_stage_N4096_R64.md"
     res = {
         "metric": metric,
