@@ -157,6 +157,15 @@ def josephson_workload_name(args, w):
     return name
 
 
+def kuramoto_workload_name(workload, euler, n_osc, replicas):
+    if workload.startswith("kuramoto-general"):
+        kind = "bf16_tcgen05" if workload == "kuramoto-general" else "fp32_cudacore"
+        return "kuramoto_general_%s_N%d_R%d" % (kind, n_osc, replicas)
+    form = "fig4_meanfield_grid" if workload == "kuramoto-fig4" else workload.split("-")[1]
+    suffix = "_euler_prog2" if euler and workload == "kuramoto-pairwise" else ""
+    return "kuramoto_%s_N%d_R%d%s" % (form, n_osc, replicas, suffix)
+
+
 def josephson_sizes(w):
     return {"points": len(w["points"]), "total_paths": int(w["paths"].sum()),
             "path_steps": float((w["paths"] * w["steps"]).sum()), "steps_per_period": w["steps_per_period"]}
@@ -348,8 +357,7 @@ def run_ours(args, rank, world, device):
             flop_per_unit = PAPER_FLOP_PAIR
             launches_per_step = 2 * S + S // w["sample_every"] + 4
             flop_per_launch = flop_per_unit * w["n_osc"] ** 2 * w["replicas"]  # one stage launch
-        cfg = {"workload": "kuramoto_%s_N%d_R%d%s" % ("fig4_meanfield_grid" if fig4 else args.workload.split("-")[1],
-                                                      w["n_osc"], w["replicas"], "_euler_prog2" if euler else ""),
+        cfg = {"workload": kuramoto_workload_name(args.workload, euler, w["n_osc"], w["replicas"]),
                "steps_per_bench_step": S, "K": w["K"], "D": w["D"], "dt": w["dt"],
                "tuning": dict(zip(("block_threads", "oscillators_per_thread", "cluster_ctas"), ens.tuning())),
                "l2": "flushed between steps (256 MiB write)"}
@@ -384,7 +392,7 @@ def run_ours(args, rank, world, device):
         metric = "oscillator-steps/sec"
         flop_per_launch = 2.0 * N * (2 * R) * N  # one GEMM K . [sin | cos]
         launches_per_step = 4 * S + S // w["sample_every"] + 4
-        cfg = {"workload": "kuramoto_general_%s_N%d_R%d" % ("bf16_tcgen05" if tc else "fp32_cudacore", N, R),
+        cfg = {"workload": kuramoto_workload_name(args.workload, False, N, R),
                "stage": "fused into the GEMM epilogue" if args.fused else "separate kernel",
                "steps_per_bench_step": S, "K0": w["K0"], "D": w["D"], "dt": w["dt"],
                "gemm": "M=%d N=%d K=%d per stage, 2 per step" % (N, 2 * R, N),
@@ -710,6 +718,14 @@ def reference_config(args, sample):
         w = {"sweep": lambda: sweep_workload(0, args), "plain": lambda: plain_workload(0),
              "fig2": lambda: fig2_workload(0)}[args.workload]()
         return {"workload": josephson_workload_name(args, w), **josephson_sizes(w), "sample": sample}
+    if args.workload.startswith("kuramoto"):
+        import inspect
+        build = {"kuramoto-fig4": inputs.kuramoto_fig4, "kuramoto-general": inputs.kuramoto_general,
+                 "kuramoto-general-fp32": inputs.kuramoto_general}.get(args.workload, inputs.kuramoto_uniform)
+        prm = inspect.signature(build).parameters  # the default sizes, without building the inputs
+        replicas = prm["replicas"].default if "replicas" in prm else 1
+        return {"workload": kuramoto_workload_name(args.workload, args.euler, prm["n_osc"].default, replicas),
+                "sample": sample}
     return {"workload": args.workload, "sample": sample}
 
 
