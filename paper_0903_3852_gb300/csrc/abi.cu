@@ -297,7 +297,8 @@ sde_status jj_autotune(sde_ctx *c) {
   return st;
 }
 
-sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
+// Host-side checks of a Josephson configuration (no CUDA call).
+sde_status validate_josephson(const sde_config *cfg) {
   SDE_CHECK_ARG(cfg->n_points >= 1, "n_points must be >= 1");
   SDE_CHECK_ARG(cfg->points && cfg->paths && cfg->steps, "points/paths/steps must be non-NULL");
   SDE_CHECK_ARG(cfg->steps_per_period >= 1 && cfg->steps_per_period <= 4096,
@@ -312,13 +313,8 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
                     cfg->paths_per_thread == 4 || cfg->paths_per_thread == 11 || cfg->paths_per_thread == 12 ||
                     cfg->paths_per_thread == 14,
                 "paths_per_thread must be 0, 1, 2, 4, 11, 12 or 14");
-  c->n_points = cfg->n_points;
-  c->P = cfg->steps_per_period;
-  c->paths.resize(c->n_points);
-  c->steps.resize(c->n_points);
-  c->offsets.resize(c->n_points);
   int64_t off = 0;
-  for (int p = 0; p < c->n_points; ++p) {
+  for (int p = 0; p < cfg->n_points; ++p) {
     const sde_jj_point &q = cfg->points[p];
     SDE_CHECK_ARG(isfinite(q.gamma) && isfinite(q.a) && isfinite(q.omega) && isfinite(q.f) &&
                       isfinite(q.D),
@@ -328,13 +324,28 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
     SDE_CHECK_ARG(q.D >= 0.0, "D must be >= 0");
     SDE_CHECK_ARG(cfg->paths[p] >= 0 && cfg->paths[p] < (1ll << 31), "paths out of range");
     SDE_CHECK_ARG(cfg->steps[p] >= 0 && cfg->steps[p] <= (1ll << 33), "steps out of range");
+    off += cfg->paths[p];
+  }
+  SDE_CHECK_ARG(off < (1ll << 40), "total paths too large");
+  return SDE_OK;
+}
+
+sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
+  const sde_status vs = validate_josephson(cfg);
+  if (vs != SDE_OK) return vs;
+  c->n_points = cfg->n_points;
+  c->P = cfg->steps_per_period;
+  c->paths.resize(c->n_points);
+  c->steps.resize(c->n_points);
+  c->offsets.resize(c->n_points);
+  int64_t off = 0;
+  for (int p = 0; p < c->n_points; ++p) {
     c->paths[p] = cfg->paths[p];
     c->steps[p] = cfg->steps[p];
     c->offsets[p] = off;
     off += cfg->paths[p];
   }
   c->total_paths = off;
-  SDE_CHECK_ARG(off < (1ll << 40), "total paths too large");
   SDE_CUDA_TRY(jj_configure());
 
   sde_jj_point *pts = nullptr;
@@ -413,6 +424,23 @@ sde_status sde_create(const sde_config *cfg, sde_ctx **out) {
   }
   *out = nullptr;
   SDE_CHECK_ARG(cfg != nullptr, "cfg is NULL");
+  // the configuration is checked on the host before any CUDA call
+  sde_status vs = SDE_OK;
+  switch (cfg->model) {
+    case SDE_JOSEPHSON:
+      vs = validate_josephson(cfg);
+      break;
+    case SDE_KURAMOTO_MEANFIELD:
+    case SDE_KURAMOTO_PAIRWISE:
+    case SDE_KURAMOTO_GENERAL:
+    case SDE_KURAMOTO_GENERAL_FP32:
+      vs = kuramoto_validate(cfg);
+      break;
+    default:
+      set_error("invalid argument: unknown model");
+      vs = SDE_ERR_INVALID_ARG;
+  }
+  if (vs != SDE_OK) return vs;
   sde_ctx *c = new (std::nothrow) sde_ctx();
   if (!c) {
     set_error("host allocation failed");

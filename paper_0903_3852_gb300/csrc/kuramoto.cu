@@ -1175,8 +1175,7 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
   return st;
 }
 
-sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, KuramotoCtx **out) {
-  *out = nullptr;
+sde_status kuramoto_validate(const sde_config *cfg) {
   SDE_CHECK_ARG(cfg->n_osc >= 1, "n_osc must be >= 1");
   SDE_CHECK_ARG(cfg->n_replicas >= 1 && cfg->n_replicas <= 65535, "n_replicas must be in [1, 65535]");
   SDE_CHECK_ARG(isfinite(cfg->K) && isfinite(cfg->D) && isfinite(cfg->dt), "K, D, dt must be finite");
@@ -1203,6 +1202,15 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   if (grid_forced)
     SDE_CHECK_ARG(cfg->cluster_ctas == 0 && cfg->block_threads == 0,
                   "the grid-wide mean field takes cluster_ctas = 0 and block_threads = 0");
+  return SDE_OK;
+}
+
+sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, KuramotoCtx **out) {
+  *out = nullptr;
+  const sde_status vs = kuramoto_validate(cfg);
+  if (vs != SDE_OK) return vs;
+  const bool mf = cfg->model == SDE_KURAMOTO_MEANFIELD;
+  const bool grid_forced = mf && (cfg->schedule == SDE_SCHED_GRID || cfg->n_osc > 8192);
   KuramotoCtx *k = new (std::nothrow) KuramotoCtx();
   if (!k) {
     set_error("host allocation failed");

@@ -11,6 +11,9 @@ namespace sde {
 
 struct KuramotoCtx;
 
+// Host-side checks of a Kuramoto configuration (no CUDA call); kuramoto_create
+// runs them first as well.
+sde_status kuramoto_validate(const sde_config *cfg);
 sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, KuramotoCtx **out);
 // Advance and reduce; (re)allocates the observables buffer *obs if it has
 // fewer than the run's sample rows.  ev0/ev1 bracket the dominant kernels.

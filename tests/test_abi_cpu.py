@@ -93,3 +93,72 @@ def test_validation_before_any_cuda_call(L):
     assert L.sde_josephson_run_fp64(ctypes.byref(pt), 100, 0, 10, 1, 0, 0, 10, None, None, None, None, None,
                                     None, None, None) == 0  # no paths: nothing to do
     L.sde_destroy(None)  # NULL-safe
+
+
+FIG2 = dict(gamma=0.9, a=4.2, omega=4.9, f=0.1, D=1e-3)
+
+
+def _create_status(make):
+    """Status of sde_create for a configuration built by `make` (0 if created)."""
+    try:
+        e = make()
+    except sde.SDEError as err:
+        return err.status, str(err)
+    del e
+    return sde.SDE_OK, ""
+
+
+@pytest.mark.parametrize("kw,field", [
+    (dict(points=[], paths=[], steps=[]), "n_points"),
+    (dict(steps_per_period=0), "steps_per_period"),
+    (dict(steps_per_period=4097), "steps_per_period"),
+    (dict(schedule=7), "schedule"),
+    (dict(block_threads=48), "block_threads"),
+    (dict(block_threads=1024), "block_threads"),
+    (dict(paths_per_thread=3), "paths_per_thread"),
+    (dict(paths_per_thread=24), "paths_per_thread"),
+    (dict(points=[dict(FIG2, omega=0.0)]), "omega"),
+    (dict(points=[dict(FIG2, gamma=-1.0)]), "gamma"),
+    (dict(points=[dict(FIG2, D=-1e-3)]), "D"),
+    (dict(points=[dict(FIG2, a=float("nan"))]), "finite"),
+    (dict(paths=[-1]), "paths"),
+    (dict(steps=[(1 << 33) + 1]), "steps"),
+])
+def test_josephson_config_is_checked_before_any_cuda_call(L, kw, field):
+    # the checks run on the host first, so they answer the same with or
+    # without a GPU
+    args = dict(points=[FIG2], paths=[64], steps=[100], steps_per_period=200)
+    args.update(kw)
+    pts, paths, steps, P = args.pop("points"), args.pop("paths"), args.pop("steps"), args.pop("steps_per_period")
+    status, msg = _create_status(lambda: sde.Ensemble.josephson(pts, paths, steps, 0, steps_per_period=P, **args))
+    assert status == sde.SDE_ERR_INVALID_ARG and field in msg, (status, msg)
+
+
+@pytest.mark.parametrize("kw,status,field", [
+    (dict(n_osc=0), sde.SDE_ERR_INVALID_ARG, "n_osc"),
+    (dict(n_replicas=0), sde.SDE_ERR_INVALID_ARG, "n_replicas"),
+    (dict(dt=0.0), sde.SDE_ERR_INVALID_ARG, "dt"),
+    (dict(D=-0.1), sde.SDE_ERR_INVALID_ARG, "D"),
+    (dict(K=float("inf")), sde.SDE_ERR_INVALID_ARG, "finite"),
+    (dict(flags=sde.SDE_FLAG_EULER), sde.SDE_ERR_UNSUPPORTED, "Euler"),
+    (dict(schedule=sde.SDE_SCHED_GRID, cluster_ctas=2), sde.SDE_ERR_INVALID_ARG, "grid-wide"),
+])
+def test_kuramoto_config_is_checked_before_any_cuda_call(L, kw, status, field):
+    args = dict(n_osc=1024, n_replicas=4, K=2.0, D=0.05, dt=0.01)
+    args.update(kw)
+    got, msg = _create_status(lambda: sde.Ensemble.kuramoto(
+        sde.SDE_KURAMOTO_MEANFIELD, args.pop("n_osc"), args.pop("n_replicas"), args.pop("K"), args.pop("D"),
+        args.pop("dt"), 0, **args))
+    assert got == status and field in msg, (got, msg)
+
+
+def test_valid_configs_pass_the_host_checks(L):
+    # a valid configuration gets past validation: with a GPU it is created,
+    # without one the first CUDA call fails instead
+    ok = (sde.SDE_OK, sde.SDE_ERR_CUDA)
+    st, msg = _create_status(lambda: sde.Ensemble.josephson([FIG2], [64], [100], 0, steps_per_period=200,
+                                                            paths_per_thread=14))
+    assert st in ok, msg
+    st, msg = _create_status(lambda: sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_PAIRWISE, 1024, 4, 2.0, 0.05, 0.01, 0,
+                                                           flags=sde.SDE_FLAG_EULER))
+    assert st in ok, msg
