@@ -186,8 +186,10 @@ typedef struct sde_ctx sde_ctx; /* opaque, library-owned */
  * block_threads or paths_per_thread is 0, autotune the launch shape by
  * timing short runs of each candidate on the current device.  The context
  * is bound to the current CUDA device.
- * Errors: SDE_ERR_INVALID_ARG (bad sizes or parameters), SDE_ERR_NO_MEMORY,
- * SDE_ERR_CUDA.  On error *out is NULL.
+ * Errors: SDE_ERR_INVALID_ARG (bad sizes or parameters) and
+ * SDE_ERR_UNSUPPORTED (a flag the model does not implement) are found on the
+ * host before any CUDA call, so they are reported the same with or without a
+ * GPU; then SDE_ERR_NO_MEMORY, SDE_ERR_CUDA.  On error *out is NULL.
  */
 sde_status sde_create(const sde_config *cfg, sde_ctx **out);
 
