@@ -22,6 +22,11 @@
 // summed in FP32 over blocks of 64 steps (aligned to absolute step indices)
 // and flushed into an FP64 per-path accumulator; per-warp moments of the
 // per-path averages are FP64.
+//
+// A thread advances one, two or four paths; with two or four, pairs of paths
+// share Blackwell's packed FP32x2 FMA, add and multiply (jj_step2,
+// box_muller_tab2), which round exactly like the scalar instructions, so
+// every launch variant produces the same bits.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -33,7 +38,6 @@
 
 namespace sde {
 namespace {
-
 
 // A - 2 pi cos(2 pi x) for |x| < 2^22 without branches: with r = x - rint(x)
 // in [-1/2, 1/2] and b = 1/4 - |r| in [-1/4, 1/4], cos(2 pi x) = sin(2 pi b),
