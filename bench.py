@@ -71,7 +71,9 @@ def parse():
     ap.add_argument("--points", type=int, default=0, help="sweep: keep only the first N points")
     ap.add_argument("--steps-cap", type=int, default=0, help="sweep: cap every point's step count")
     ap.add_argument("--block", type=int, default=0, help="fixed threads per block (skips autotuning)")
-    ap.add_argument("--ilp", type=int, default=0, help="fixed paths per thread (skips autotuning)")
+    ap.add_argument("--ilp", type=int, default=0,
+                    help="fixed Josephson launch variant, skipping the autotuner: 1, 2 or 4 paths per "
+                         "thread, 11 / 12 / 14 the same with fewer registers")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fused", action="store_true",
                     help="general coupling, tensor-core form: SRK2 sub-steps in the GEMM epilogue")
