@@ -311,7 +311,7 @@ sde_status sde_box_muller_words(const uint32_t *w_dev, int64_t n_pairs, int32_t 
                                 void *stream);
 
 /*
- * Allocation-free run of one Eq. 1 parameter point.  The paper has no
+ * Allocation-free run of one Josephson parameter point.  The paper has no
  * counterpart: this is an interface for callers that must not allocate
  * device memory -- code running inside another framework's memory pool or
  * arena, which forbids allocations it does not manage; code invoked while a
@@ -330,7 +330,10 @@ sde_status sde_box_muller_words(const uint32_t *w_dev, int64_t n_pairs, int32_t 
  *  - n_paths above SDE_NOALLOC_MAX_PATHS returns SDE_ERR_INVALID_ARG.
  *  - The first call on each device looks up that array's device address
  *    (cudaGetSymbolAddress, with that device current); make the first call
- *    on a device before any stream capture begins.
+ *    on a device before any stream capture begins.  The address is kept for
+ *    the life of the process, so resetting the device (cudaDeviceReset, or
+ *    anything else that destroys its primary context) between calls is not
+ *    supported.
  *  - All calls on a device share the array.  Calls that can overlap on the
  *    GPU (different streams without ordering, or host threads) race on it
  *    and must be serialised by the caller.  Each call writes every entry it
@@ -428,6 +431,21 @@ sde_status sde_mlp_train_step(sde_mlp *mlp, const float *X_dev, const float *y_d
    X_dev [n_members][B][n_in], y_dev [n_members][B] */
 sde_status sde_mlp_train_step_members(sde_mlp *mlp, const float *X_dev, const float *y_dev, int64_t B,
                                       float *loss_dev, void *stream);
+
+/*
+ * FP32 fused-multiply-add throughput probe (measurement infrastructure; the
+ * paper has no counterpart).  Launches `grid` blocks of `block` threads
+ * (block a multiple of 32, at most 256), each thread running eight
+ * independent chains a <- 0.999 a + 0.001 for 16 * iters rounds: scalar FFMA
+ * (packed = 0) or Blackwell's two-wide FFMA2 (packed = 1, two FMAs per
+ * lane-instruction).  *flop_host (nullable) receives the FLOP the launch
+ * executes (2 per FMA); the caller times the launch on `stream` with events
+ * to obtain the FP32 peak that the integration kernels' rooflines use.
+ * sink_dev: caller-owned device array of grid * block floats (written).
+ * Errors: SDE_ERR_INVALID_ARG before any CUDA call; SDE_ERR_CUDA.
+ */
+sde_status sde_fp32_fma_probe(int32_t packed, int64_t iters, int32_t grid, int32_t block, float *sink_dev,
+                              double *flop_host, void *stream);
 
 /* Version of this ABI (major * 100 + minor). */
 int32_t sde_abi_version(void);

@@ -117,6 +117,8 @@ SIGNATURES = [
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_int64, ctypes.c_int64] + [_VP] * 9 + [_VP]),
     ("sde_box_muller_words", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
+    ("sde_fp32_fma_probe", ctypes.c_int,
+     [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     ("sde_josephson_run_fp64", ctypes.c_int,
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64] + [_VP] * 7 + [_VP]),
@@ -317,14 +319,49 @@ class Ensemble:
         self.close()
 
 
+def _check_buffers(named):
+    """Each (name, tensor, dtype, n) must be a contiguous tensor of that dtype
+    with at least n elements on the current CUDA device; raises ValueError
+    before anything reaches the GPU (sizes first, then types, then devices)."""
+    import torch
+    for name, t, dtype, n in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.numel() < n:
+            raise ValueError("%s holds %d elements, fewer than the %d required" % (name, t.numel(), n))
+    for name, t, dtype, n in named:
+        if t.dtype != dtype:
+            raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    for name, t, dtype, n in named:
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError("%s must be on the current CUDA device, got %s" % (name, t.device))
+
+
 def josephson_run_noalloc(point, steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
                           x_in, v_in, x_out, v_out, w_out, vsum_out, obs_out, w_in=None, vsum_in=None,
                           stream=None):
     """sde_josephson_run_noalloc: one parameter point, no device allocation by the
     library (scratch lives in a fixed static array of NOALLOC_MAX_PATHS / 32
     partials).  obs_out: a CUDA tensor of 5 float64 (one sde_obs_row)."""
+    import torch
+    # The C entry point sees bare pointers and cannot check buffer sizes: a
+    # short or mistyped buffer would be read or written past its end on the
+    # GPU, so every buffer is checked here before the call.
+    n = int(n_paths)
+    if n < 0:
+        raise ValueError("n_paths must be >= 0")
+    need = [("x_in", x_in, torch.float32, n), ("v_in", v_in, torch.float32, n),
+            ("x_out", x_out, torch.float32, n), ("v_out", v_out, torch.float32, n),
+            ("w_out", w_out, torch.int32, n), ("vsum_out", vsum_out, torch.float64, n),
+            ("obs_out", obs_out, torch.float64, 5)]
+    if w_in is not None:
+        need.append(("w_in", w_in, torch.int32, n))
+    if vsum_in is not None:
+        need.append(("vsum_in", vsum_in, torch.float64, n))
+    _check_buffers(need)
     p = JJPoint(point["gamma"], point["a"], point["omega"], point["f"], point["D"])
-    assert obs_out.numel() * obs_out.element_size() >= ctypes.sizeof(ObsRow)
     _check(lib().sde_josephson_run_noalloc(
         ctypes.byref(p), steps_per_period, n_paths, total_steps, seed, n_begin, n_end,
         _ptr(x_in), _ptr(v_in), _ptr(w_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(w_out),
@@ -353,6 +390,17 @@ def josephson_run_fp64(point, steps_per_period, total_steps, seed, n_begin, n_en
         ctypes.byref(p), steps_per_period, x_in.numel(), total_steps, seed, point_index, n_begin, n_end,
         _ptr(x_in), _ptr(v_in), _ptr(vsum_in), _ptr(x_out), _ptr(v_out), _ptr(vsum_out), _ptr(err),
         _stream(stream)))
+
+
+def fp32_fma_probe(packed, iters, grid, block, sink, stream=None):
+    """sde_fp32_fma_probe: launch the FP32 FMA throughput probe on `stream`;
+    sink is a float32 CUDA tensor of at least grid * block elements.  Returns
+    the FLOP the launch executes."""
+    import torch
+    assert sink.dtype == torch.float32 and sink.numel() >= grid * block
+    flop = ctypes.c_double()
+    _check(lib().sde_fp32_fma_probe(packed, iters, grid, block, _ptr(sink), ctypes.byref(flop), _stream(stream)))
+    return flop.value
 
 
 SURROGATE_BOX = ((0.0, 8.0), (1.0, 10.0), (0.0, 1.0), (0.5, 2.0), (-4.0, -1.0))  # a, omega, f, gamma, log10 D

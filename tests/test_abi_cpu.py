@@ -162,3 +162,36 @@ def test_valid_configs_pass_the_host_checks(L):
     st, msg = _create_status(lambda: sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_PAIRWISE, 1024, 4, 2.0, 0.05, 0.01, 0,
                                                            flags=sde.SDE_FLAG_EULER))
     assert st in ok, msg
+
+
+def test_noalloc_wrapper_checks_buffers_before_the_call():
+    """sde_josephson_run_noalloc sees bare pointers, so its binding checks every
+    buffer's length, dtype and device first: a short or mistyped buffer raises
+    on the host and nothing is launched (CPU tensors: no GPU involved)."""
+    import torch
+    pt = dict(gamma=0.9, a=4.2, omega=4.9, f=0.1, D=1e-3)
+    n = 64
+    f32 = lambda k: torch.zeros(k, dtype=torch.float32)  # noqa: E731
+    good = dict(x_in=f32(n), v_in=f32(n), x_out=f32(n), v_out=f32(n),
+                w_out=torch.zeros(n, dtype=torch.int32), vsum_out=torch.zeros(n, dtype=torch.float64),
+                obs_out=torch.zeros(5, dtype=torch.float64))
+
+    def call(**over):
+        b = dict(good, **over)
+        sde.josephson_run_noalloc(pt, 200, n, 100, 0, 0, 100, b["x_in"], b["v_in"], b["x_out"], b["v_out"],
+                                  b["w_out"], b["vsum_out"], b["obs_out"], w_in=b.get("w_in"),
+                                  vsum_in=b.get("vsum_in"))
+
+    with pytest.raises(ValueError, match="fewer than"):
+        call(v_out=f32(n - 1))
+    with pytest.raises(ValueError, match="fewer than"):
+        call(vsum_in=torch.zeros(3, dtype=torch.float64))
+    with pytest.raises(ValueError, match="must be torch.int32"):
+        call(w_out=torch.zeros(n, dtype=torch.int64))
+    with pytest.raises(ValueError, match="must be torch.float64"):
+        call(vsum_out=torch.zeros(n, dtype=torch.float32))
+    with pytest.raises(ValueError, match="fewer than"):
+        call(obs_out=torch.zeros(4, dtype=torch.float64))
+    # right sizes and types, but host memory: refused before the C call
+    with pytest.raises(ValueError, match="current CUDA device"):
+        call()

@@ -9,6 +9,8 @@ shared by every call, so the second call checks that what the first call left
 there does no harm.  This file is collected last so that a failure here stops
 a -x run only after every other test has run.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -62,11 +64,16 @@ def test_noalloc_matches_regular_entry_point_twice():
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
-    ensure_built()
-    point = dict(gamma=0.9, a=4.2, omega=4.9, f=0.1, D=1e-3)
-    n = sde.NOALLOC_MAX_PATHS + 1
+    """The C entry point itself refuses more paths than its static array covers,
+    before it touches any buffer (called through ctypes directly: the Python
+    wrapper would already refuse the undersized buffers passed here)."""
+    L = ensure_built()
+    p = sde.JJPoint(0.9, 4.2, 4.9, 0.1, 1e-3)
     t = torch.empty(1, device="cuda")
-    with pytest.raises(sde.SDEError) as e:
-        sde.josephson_run_noalloc(point, P, n, 10, 0, 0, 10, t, t, t, t, t, t,
-                                  torch.empty(5, dtype=torch.float64, device="cuda"))
-    assert e.value.status == 1 and "at most" in str(e.value)
+    obs = torch.empty(5, dtype=torch.float64, device="cuda")
+    ptr = t.data_ptr()
+    st = L.sde_josephson_run_noalloc(ctypes.byref(p), P, sde.NOALLOC_MAX_PATHS + 1, 10, 0, 0, 10,
+                                     ptr, ptr, None, None, ptr, ptr, ptr, ptr, obs.data_ptr(),
+                                     torch.cuda.current_stream().cuda_stream)
+    assert st == sde.SDE_ERR_INVALID_ARG
+    assert "at most" in L.sde_last_error().decode()
