@@ -32,6 +32,7 @@ def lib():
         path = _build.build()
         L = ctypes.CDLL(path)
         L.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.oracle_philox4x32_rounds.argtypes = [_u32p, _u32p, ctypes.c_int, _u32p]
         L.oracle_uniform.argtypes = [ctypes.c_uint32]
         L.oracle_uniform.restype = ctypes.c_double
         L.oracle_box_muller.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _f64p, _f64p]
@@ -85,6 +86,19 @@ def philox4x32_10(ctr, key):
     kp = key.ctypes.data_as(_u32p)
     for i in range(ctr.shape[0]):
         L.oracle_philox4x32_10(ctr[i].ctypes.data_as(_u32p), kp, out[i].ctypes.data_as(_u32p))
+    return out
+
+
+def philox4x32_rounds(ctr, key, rounds):
+    """The first `rounds` rounds of Philox4x32 (SC'11, Sec. 4): one counter
+    (4,) uint32 and key (2,) uint32 -> (4,) uint32.  rounds = 10 equals
+    philox4x32_10; fewer rounds expose the round function and the key
+    schedule to tests."""
+    ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(4))
+    key = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+    out = np.empty(4, dtype=np.uint32)
+    lib().oracle_philox4x32_rounds(ctr.ctypes.data_as(_u32p), key.ctypes.data_as(_u32p), int(rounds),
+                                   out.ctypes.data_as(_u32p))
     return out
 
 

@@ -44,13 +44,16 @@
 /* c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is bumped by  */
 /* the Weyl constants between rounds.                                   */
 /* ------------------------------------------------------------------ */
-void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
-                          uint32_t out[4]) {
+/* The first `rounds` rounds (Philox4x32-R); R = 10 is the generator used
+ * everywhere.  Fewer rounds exist only so that tests can read the round
+ * function and key schedule off known inputs. */
+void oracle_philox4x32_rounds(const uint32_t ctr[4], const uint32_t key[2],
+                              int rounds, uint32_t out[4]) {
   const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
   const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
   uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
   uint32_t k0 = key[0], k1 = key[1];
-  for (int round = 0; round < 10; ++round) {
+  for (int round = 0; round < rounds; ++round) {
     uint64_t p0 = M0 * (uint64_t)c[0];
     uint64_t p1 = M1 * (uint64_t)c[2];
     uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
@@ -62,6 +65,11 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
     k1 += W1;
   }
   memcpy(out, c, sizeof c);
+}
+
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                          uint32_t out[4]) {
+  oracle_philox4x32_rounds(ctr, key, 10, out);
 }
 
 /* Uniform variate from one 32-bit word: the top 24 bits, shifted into

@@ -1,8 +1,10 @@
 """Pins of the oracle's noise generator (CPU only).
 
 Philox4x32-10 (Salmon et al., SC'11) is pinned to an independent implementation,
-cuRAND's host-side Philox4_32_10 generator, and to the sensitivity of every
-output word to every counter and key word; the uniform map and Box-Muller (Sec. 4.1: two uniforms -> two
+cuRAND's host-side Philox4_32_10 generator, to its round function and key
+schedule read off zero inputs (Weyl constants from their closed forms, the
+published multipliers), and to the sensitivity of every output word to every
+counter and key word; the uniform map and Box-Muller (Sec. 4.1: two uniforms -> two
 Gaussians) to closed-form values and to the moments of the standard normal.
 """
 import math
@@ -16,13 +18,49 @@ import curand_ref
 import oracle
 
 
-@pytest.mark.skipif(not curand_ref.available(), reason="libcurand not found")
 @pytest.mark.parametrize("seed,b0,n", curand_ref.CASES)
 def test_philox_matches_curand_host_generator(seed, b0, n):
     # an independent implementation of Philox4x32-10: cuRAND's generator
-    # (host side), at the counters its default ordering is documented to use
+    # (host side), at the counters its default ordering is documented to use.
+    # libcurand ships with the CUDA toolkit this project builds with; its
+    # absence is a failure here, not a reason to skip the pin.
+    assert curand_ref.available(), "libcurand (CUDA toolkit) not found: the external Philox pin cannot run"
     got = oracle.philox4x32_10(curand_ref.counters(b0, n), oracle.seed_key(seed))
     assert np.array_equal(got, curand_ref.blocks(seed, b0, n))
+
+
+def test_philox_round_function_and_key_schedule_from_definitions():
+    """Philox4x32 (Salmon et al., SC'11, Sec. 4) read off zero inputs, with no
+    other implementation involved.  A round maps c to (hi(M1 c2) ^ c1 ^ k0,
+    lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)) and then adds the Weyl constants
+    to the key.  From c = 0 the products vanish, so one round returns the key
+    in words 0 and 2; from c = 0 and k = 0, two rounds return (W0, 0, W1, 0);
+    the third round multiplies W0 by M0 and W1 by M1, so M0 and M1 are the
+    exact quotients of the 64-bit products it leaves behind.  The Weyl
+    constants are defined as the leading 32 bits of the golden ratio's
+    fractional part and of sqrt(3) - 1; the multipliers are the published
+    0xD2511F53 and 0xCD9E8D57.  A wrong constant, a swapped word or a key bump
+    in the wrong place fails here."""
+    from math import isqrt
+    w0 = (isqrt(5 << 64) - (1 << 32)) // 2  # floor(2^32 (sqrt(5) - 1) / 2)
+    w1 = isqrt(3 << 64) - (1 << 32)  # floor(2^32 (sqrt(3) - 1))
+    z = [0, 0, 0, 0]
+    k = [0x01234567, 0x89ABCDEF]
+    assert list(oracle.philox4x32_rounds(z, k, 1)) == [k[0], 0, k[1], 0]
+    assert list(oracle.philox4x32_rounds(z, [0, 0], 2)) == [w0, 0, w1, 0]
+    r3 = [int(x) for x in oracle.philox4x32_rounds(z, [0, 0], 3)]
+    k3 = [(2 * w0) & 0xFFFFFFFF, (2 * w1) & 0xFFFFFFFF]  # key of the third round
+    p1 = ((r3[0] ^ k3[0]) << 32) | r3[1]  # M1 * W1
+    p0 = ((r3[2] ^ k3[1]) << 32) | r3[3]  # M0 * W0
+    assert p0 % w0 == 0 and p1 % w1 == 0
+    assert (p0 // w0, p1 // w1) == (0xD2511F53, 0xCD9E8D57)
+    # the generator is ten of these rounds
+    rng = np.random.default_rng(9)
+    for _ in range(20):
+        c = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        kk = rng.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+        assert np.array_equal(oracle.philox4x32_rounds(c, kk, 10), oracle.philox4x32_10(c, kk)[0])
+        assert not np.array_equal(oracle.philox4x32_rounds(c, kk, 9), oracle.philox4x32_10(c, kk)[0])
 
 
 def test_philox_counter_sensitivity():
