@@ -209,13 +209,41 @@ sde_status sde_run_ensemble(sde_ctx *ctx, const sde_run_desc *run, void *stream)
  * run to rows_host: one row per point (Josephson) or per sample time
  * (Kuramoto).  *n_rows receives the row count; if capacity is smaller, only
  * the first `capacity` rows are copied.  Returns the latched device status
- * (SDE_ERR_NUMERIC, SDE_ERR_TIMEOUT) if a kernel reported one.
+ * (SDE_ERR_TIMEOUT before SDE_ERR_NUMERIC) if a kernel reported one since the
+ * last call; a reported status is cleared, so later runs start clean.
  */
 sde_status sde_observables(sde_ctx *ctx, sde_obs_row *rows_host, int64_t capacity,
                            int64_t *n_rows);
 
 /* Free the context and its workspace.  NULL-safe.  Synchronises the device. */
 void sde_destroy(sde_ctx *ctx);
+
+/*
+ * Failure detection (the paper has no counterpart).  Kernels that wait on
+ * other threads through mbarriers -- the tensor-core GEMM of
+ * SDE_KURAMOTO_GENERAL (its TMA producer and MMA issuer) and the Kuramoto
+ * mean field with SDE_FLAG_ASYNC_EXCHANGE -- bound every such wait by a
+ * limit of the GPU's nanosecond timer.  When one expires the kernel stops
+ * issuing work, drains what it has issued (with waits of at most one second,
+ * whatever the limit), latches SDE_ERR_TIMEOUT for the next sde_observables
+ * and returns; the context stays usable.  This sets the limit for the
+ * context's later launches: ns = 0 restores the default of one second.  A
+ * small limit makes the waits expire on purpose, for tests of that path.
+ * Josephson contexts have no such waits (the call succeeds and changes
+ * nothing).  Errors: SDE_ERR_INVALID_ARG (NULL ctx).
+ */
+sde_status sde_set_wait_limit(sde_ctx *ctx, uint64_t ns);
+
+/*
+ * Allocation-failure injection for tests (the paper has no counterpart):
+ * during the next sde_create or sde_mlp_create call, its nth allocation
+ * (1 = the host context of sde_create, then the device buffers in the order
+ * the call makes them, its autotuning scratch included) fails as if memory
+ * had run out, so the call returns SDE_ERR_NO_MEMORY, frees what it had
+ * allocated and leaves *out NULL.  Each create call disarms the injection
+ * when it returns; nth <= 0 disarms it now.  Process-wide.
+ */
+void sde_debug_fail_allocation(int32_t nth);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *sde_last_error(void);
@@ -415,13 +443,28 @@ sde_status sde_mlp_get_params(sde_mlp *mlp, int32_t member, float *params_dev, v
 sde_status sde_mlp_features(sde_mlp *mlp, const sde_jj_point *points_dev, int64_t n, float *X_dev,
                             void *stream);
 /* forward pass of every member: mean_dev[b] = ensemble mean, spread_dev[b]
-   = ensemble standard deviation (NULL allowed); X_dev [B][n_in] FP32 */
+   = ensemble standard deviation (NULL allowed); X_dev [B][n_in] FP32.
+   Networks of width 256 with 2..8 hidden layers and n_in <= 8 run one fused
+   tensor-core kernel (the square hidden layers as tcgen05 MMAs of 128 points
+   x 256 x 256 with BF16 operands and FP32 accumulators in tensor memory, the
+   bias, SiLU and output layer in their epilogues); other shapes, or after
+   sde_mlp_use_tensor_cores(mlp, 0), the CUDA-core kernels of the training
+   path.  Asynchronous; an expired device wait of the tensor-core kernel is
+   reported by sde_mlp_check. */
 sde_status sde_mlp_forward(sde_mlp *mlp, const float *X_dev, int64_t B, float *mean_dev,
                            float *spread_dev, void *stream);
 /* gradient of the mean-squared error of one member: grad_dev[num_params],
    loss_dev[1] (both device, FP32) */
 sde_status sde_mlp_grad(sde_mlp *mlp, int32_t member, const float *X_dev, const float *y_dev,
                         int64_t B, float *grad_dev, float *loss_dev, void *stream);
+/* select the tensor-core forward (enable != 0, the default where the shape
+   allows it) or the CUDA-core one; SDE_ERR_UNSUPPORTED if the shape has no
+   tensor-core path */
+sde_status sde_mlp_use_tensor_cores(sde_mlp *mlp, int32_t enable);
+/* synchronise the device and return SDE_ERR_TIMEOUT if a tensor-core forward
+   kernel found a bounded wait expired since the last check (the status is
+   then cleared; the affected outputs were not written) */
+sde_status sde_mlp_check(sde_mlp *mlp);
 /* change the Adam step size (learning-rate schedules); lr > 0 */
 sde_status sde_mlp_set_lr(sde_mlp *mlp, float lr);
 /* one Adam step of every member on the same batch; loss_dev[n_members] or NULL */

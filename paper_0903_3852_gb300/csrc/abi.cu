@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <memory>
 #include <new>
 #include <numeric>
@@ -65,13 +66,36 @@ struct sde_ctx {
   bool gvalid = false;
 };
 
+namespace sde {
+
+// Allocation-failure injection (sde_debug_fail_allocation): the number of
+// allocations still to succeed before one fails, -1 = off.
+static std::atomic<int> g_fail_countdown{-1};
+
+bool injected_alloc_failure() {
+  int n = g_fail_countdown.load();
+  while (n >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(n, n - 1)) return n == 0;
+  }
+  return false;
+}
+
+void alloc_injection_disarm() { g_fail_countdown.store(-1); }
+
+cudaError_t device_alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+}  // namespace sde
+
 namespace {
 
 template <class T>
 cudaError_t dmalloc(T **p, size_t count) {
-  *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc((void **)p, sizeof(T) * count);
+  return device_alloc((void **)p, sizeof(T) * count);
 }
 
 void free_ctx(sde_ctx *c) {
@@ -348,24 +372,28 @@ sde_status create_josephson(sde_ctx *c, const sde_config *cfg) {
   c->total_paths = off;
   SDE_CUDA_TRY(jj_configure());
 
-  sde_jj_point *pts = nullptr;
-  int64_t *steps = nullptr, *offs = nullptr, *paths = nullptr;
-  SDE_CUDA_TRY(dmalloc(&pts, c->n_points));
-  SDE_CUDA_TRY(dmalloc(&steps, c->n_points));
-  SDE_CUDA_TRY(dmalloc(&offs, c->n_points));
-  SDE_CUDA_TRY(dmalloc(&paths, c->n_points));
+  // the point and step tables are needed only by the prepare kernel: freed
+  // on every way out of this block
+  struct DevFree {
+    void operator()(void *p) const { cudaFree(p); }
+  };
+  sde_jj_point *pts_raw = nullptr;
+  int64_t *steps_raw = nullptr;
+  SDE_CUDA_TRY(dmalloc(&pts_raw, c->n_points));
+  std::unique_ptr<sde_jj_point, DevFree> pts(pts_raw);
+  SDE_CUDA_TRY(dmalloc(&steps_raw, c->n_points));
+  std::unique_ptr<int64_t, DevFree> steps(steps_raw);
+  SDE_CUDA_TRY(dmalloc(&c->offsets_dev, c->n_points));
+  SDE_CUDA_TRY(dmalloc(&c->paths_dev, c->n_points));
   SDE_CUDA_TRY(dmalloc(&c->consts, c->n_points));
   SDE_CUDA_TRY(dmalloc(&c->drive, c->P));
-  SDE_CUDA_TRY(cudaMemcpy(pts, cfg->points, sizeof(sde_jj_point) * c->n_points, cudaMemcpyHostToDevice));
-  SDE_CUDA_TRY(cudaMemcpy(steps, c->steps.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
-  SDE_CUDA_TRY(cudaMemcpy(offs, c->offsets.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
-  SDE_CUDA_TRY(cudaMemcpy(paths, c->paths.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
-  SDE_CUDA_TRY(jj_prepare(pts, c->n_points, c->P, steps, offs, paths, c->consts, c->drive, 0));
+  SDE_CUDA_TRY(cudaMemcpy(pts.get(), cfg->points, sizeof(sde_jj_point) * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(steps.get(), c->steps.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(c->offsets_dev, c->offsets.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(cudaMemcpy(c->paths_dev, c->paths.data(), 8 * c->n_points, cudaMemcpyHostToDevice));
+  SDE_CUDA_TRY(jj_prepare(pts.get(), c->n_points, c->P, steps.get(), c->offsets_dev, c->paths_dev, c->consts,
+                          c->drive, 0));
   SDE_CUDA_TRY(cudaDeviceSynchronize());
-  cudaFree(pts);
-  cudaFree(steps);
-  c->offsets_dev = offs;
-  c->paths_dev = paths;
 
   int32_t max_units = 0;
   for (int ilp : {1, 2, 4}) {
@@ -412,7 +440,7 @@ sde_status run_graph(sde_ctx *c, const sde_run_desc *r, cudaStream_t s) {
 
 extern "C" {
 
-int32_t sde_abi_version(void) { return 100; }
+int32_t sde_abi_version(void) { return 101; }
 
 const char *sde_last_error(void) { return g_last_error.c_str(); }
 
@@ -441,8 +469,9 @@ sde_status sde_create(const sde_config *cfg, sde_ctx **out) {
       vs = SDE_ERR_INVALID_ARG;
   }
   if (vs != SDE_OK) return vs;
-  sde_ctx *c = new (std::nothrow) sde_ctx();
+  sde_ctx *c = injected_alloc_failure() ? nullptr : new (std::nothrow) sde_ctx();
   if (!c) {
+    alloc_injection_disarm();
     set_error("host allocation failed");
     return SDE_ERR_NO_MEMORY;
   }
@@ -479,6 +508,7 @@ sde_status sde_create(const sde_config *cfg, sde_ctx **out) {
         st = SDE_ERR_INVALID_ARG;
     }
   }
+  alloc_injection_disarm();
   if (st != SDE_OK) {
     std::string msg = g_last_error;
     free_ctx(c);
@@ -532,6 +562,8 @@ sde_status sde_observables(sde_ctx *c, sde_obs_row *rows, int64_t capacity, int6
   if (n_rows) *n_rows = c->n_obs_rows;
   uint32_t err = 0;
   SDE_CUDA_TRY(cudaMemcpy(&err, c->err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  // a latched device status is reported once, then cleared for later runs
+  if (err) SDE_CUDA_TRY(cudaMemset(c->err, 0, sizeof(uint32_t)));
   if (err & kErrTimeout) {
     set_error("a bounded device wait expired");
     return SDE_ERR_TIMEOUT;
@@ -544,6 +576,16 @@ sde_status sde_observables(sde_ctx *c, sde_obs_row *rows, int64_t capacity, int6
 }
 
 void sde_destroy(sde_ctx *c) { free_ctx(c); }
+
+sde_status sde_set_wait_limit(sde_ctx *c, uint64_t ns) {
+  clear_error();
+  SDE_CHECK_ARG(c != nullptr, "ctx is NULL");
+  // Josephson kernels have no device waits: nothing to set there
+  if (c->kur) kuramoto_set_wait_limit(c->kur, ns == 0 ? 1000000000ull : ns);
+  return SDE_OK;
+}
+
+void sde_debug_fail_allocation(int32_t nth) { g_fail_countdown.store(nth >= 1 ? nth - 1 : -1); }
 
 sde_status sde_get_tuning(const sde_ctx *c, int32_t *block, int32_t *ilp, int32_t *cluster) {
   clear_error();

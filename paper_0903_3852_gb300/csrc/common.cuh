@@ -29,6 +29,14 @@ void clear_error();
 
 sde_status cuda_fail(cudaError_t e, const char *what);
 
+// cudaMalloc of the library's workspaces, through the allocation-failure
+// injection of sde_debug_fail_allocation.
+cudaError_t device_alloc(void **p, size_t bytes);
+// True when the injection says the allocation being made fails (abi.cu).
+bool injected_alloc_failure();
+// Disarm the injection (the end of every create call).
+void alloc_injection_disarm();
+
 #define SDE_CUDA_TRY(expr)                                    \
   do {                                                        \
     cudaError_t e_ = (expr);                                  \

@@ -28,5 +28,7 @@ void kuramoto_tuning(const KuramotoCtx *k, int32_t *block, int32_t *per_thread, 
 // run, when they were timed per launch; false if they were not.
 bool kuramoto_kernel_stats(KuramotoCtx *k, float *mean_ms, float *total_ms, int64_t *launches);
 void kuramoto_destroy(KuramotoCtx *k);
+// Limit (ns) of the bounded device waits of the context's later launches.
+void kuramoto_set_wait_limit(KuramotoCtx *k, uint64_t ns);
 
 }  // namespace sde

@@ -27,6 +27,7 @@
 #include "kuramoto_internal.h"
 #include "philox.cuh"
 #include "tc_gemm.cuh"
+#include "tma_map.h"
 
 namespace sde {
 
@@ -199,38 +200,9 @@ int grid_for(int64_t n, int sm_count) {
   return (int)std::min<int64_t>(b, (int64_t)sm_count * 16);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
-
 // 2D BF16 tensor map: rows x cols (cols contiguous), box of box_rows x 64.
 sde_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows) {
-  auto fn = encode_fn();
-  if (!fn) {
-    set_error("cuTensorMapEncodeTiled is not available from the driver");
-    return SDE_ERR_CUDA;
-  }
-  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
-    return SDE_ERR_CUDA;
-  }
-  return SDE_OK;
+  return make_map_bf16(map, base, rows, cols, box_rows);
 }
 
 struct GemmPlan {
@@ -273,7 +245,7 @@ void launch_tc(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t 
   const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
   dim3 grid(M / tc::BM, Ncols / BN);
   tc::tc_gemm_bf16_kernel<BN, EPI><<<grid, tc::EpiThreads<EPI>::value, tc::Shape<BN>::SMEM_BYTES, s>>>(
-      g->mapK, g->mapOp[which], k->P, M, Kdim, k->err, sa);
+      g->mapK, g->mapOp[which], k->P, M, Kdim, k->err, sa, k->wait_ns);
 }
 
 // GEMM reading operand buffer `which`; epi = EPI_STORE_D writes Dt, the stage
@@ -342,13 +314,13 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
     return SDE_ERR_INVALID_ARG;
   }
   cudaError_t e;
-  if ((e = cudaMalloc((void **)&k->theta_t, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  if ((e = cudaMalloc((void **)&k->g1, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  if ((e = cudaMalloc((void **)&k->P, NR * 2 * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  if ((e = cudaMalloc((void **)&k->psi4, NR * 4 * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = device_alloc((void **)&k->theta_t, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = device_alloc((void **)&k->g1, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = device_alloc((void **)&k->P, NR * 2 * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = device_alloc((void **)&k->psi4, NR * 4 * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if (is_tc(k)) {
-    if ((e = cudaMalloc((void **)&k->Kbf16, NN * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc((void **)&k->Bt, NR * 2 * 2 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = device_alloc((void **)&k->Kbf16, NN * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = device_alloc((void **)&k->Bt, NR * 2 * 2 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     GemmPlan *g = new GemmPlan();
     k->gemm_plan = g;
     g->bn = (2 * k->R) % 256 == 0 ? 256 : 128;
@@ -371,8 +343,8 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
           cudaSuccess)
         return cuda_fail(e, "cudaFuncSetAttribute");
   } else {
-    if ((e = cudaMalloc((void **)&k->Kf32, NN * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-    if ((e = cudaMalloc((void **)&k->Bt32, NR * 2 * 4 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = device_alloc((void **)&k->Kf32, NN * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    if ((e = device_alloc((void **)&k->Bt32, NR * 2 * 4 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   }
   k->block = is_tc(k) ? tc::THREADS : 256;
   k->opt = is_tc(k) ? ((GemmPlan *)k->gemm_plan)->bn : SG_BN;

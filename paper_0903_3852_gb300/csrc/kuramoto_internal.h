@@ -20,6 +20,7 @@ struct KuramotoCtx {
   uint64_t seed = 0;
   int sm_count = 0;
   uint32_t *err = nullptr;
+  uint64_t wait_ns = 1000000000ull;  // limit of the kernels' bounded device waits
   uint32_t flags = 0;
   int block = 0, opt = 0;
   int cs = 1;  // mean field: CTAs per replica (thread-block cluster size); 0 = grid-wide form
@@ -71,6 +72,7 @@ struct KurArgs {
   float sc;      // sqrt(2 D dt) / (2 pi)
   uint64_t seed;
   uint32_t *err;
+  uint64_t wait_ns;  // limit of each bounded mbarrier wait (asynchronous exchange)
 };
 
 // Arguments of one pairwise stage launch.

@@ -15,9 +15,13 @@
 //                        quarter, then either stores of Dt (each warp store
 //                        is one 128 B row segment: the TMEM lane is the row
 //                        index i) or the fused SRK2 sub-step (16 warps)
-// Every mbarrier wait is bounded (about one second of %globaltimer); on expiry
-// the CTA records SDE kErrTimeout, drains its own TMA loads and MMAs with
-// bounded waits, frees its tensor memory and returns.
+// The producer's and the MMA issuer's mbarrier waits are bounded by a limit
+// in nanoseconds of %globaltimer (a kernel argument, one second by default);
+// on expiry the CTA records kErrTimeout and stops issuing.  Whatever it did
+// issue is then drained with waits of the fixed one-second bound, whatever
+// the argument: the producer always waits for its last loads to land, and
+// every thread waits for the commit that follows the last MMA, before the
+// tensor memory is freed and the CTA returns.
 #pragma once
 
 #include <cuda.h>
@@ -66,6 +70,8 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t byte
                : "memory");
 }
 
+// One try_wait: true once the phase of `parity` has completed; may suspend
+// the thread for a while first.
 __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -78,15 +84,32 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *b, uint32_t parity) 
   return ok;
 }
 
+// The same test without suspending.
+__device__ __forceinline__ uint32_t mbar_test_wait(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
 // Wait for the phase of `parity` to complete; false if the CTA's abort flag
-// is raised or about a second passes (then the flag is raised).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag) {
-  if (mbar_try_wait(b, parity)) return true;
+// is raised or limit_ns pass (then the flag is raised).  try_wait may
+// suspend the thread longer than a short limit, so limits under a
+// millisecond poll with test_wait.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag,
+                                          uint64_t limit_ns = kTimeoutNs) {
+  const bool poll = limit_ns < 1000000ull;
+  if (poll ? mbar_test_wait(b, parity) : mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (;;) {
-    if (mbar_try_wait(b, parity)) return true;
+    if (poll ? mbar_test_wait(b, parity) : mbar_try_wait(b, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kTimeoutNs) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -275,7 +298,8 @@ struct EpiThreads {
 template <int BN, int EPI>
 __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
     tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                        float *__restrict__ Dt, int M, int Kdim, uint32_t *err, const StageArgs sa) {
+                        float *__restrict__ Dt, int M, int Kdim, uint32_t *err, const StageArgs sa,
+                        uint64_t wait_ns) {
   constexpr int NGROUPS = EpiThreads<EPI>::value / 128;  // column groups of the epilogue
   using S = Shape<BN>;
   extern __shared__ uint8_t smem_raw[];
@@ -322,14 +346,18 @@ __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) break;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wait_ns)) break;
       mbar_arrive_expect_tx(&full_bar[s], (uint32_t)S::STAGE_BYTES);
       tma_load_2d(smA + s * S::A_BYTES, &mapA, &full_bar[s], kb * BK, m0);
       tma_load_2d(smB + s * S::B_BYTES, &mapB, &full_bar[s], kb * BK, n0);
       issued = kb + 1;
     }
-    if (abort_flag) {
-      // drain this CTA's own loads still in flight (bounded)
+    {
+      // Wait until this CTA's own loads have landed before anyone may free the
+      // CTA: the MMA issuer can give up on a load after the last one was
+      // issued.  Loads older than the last STAGES were consumed by MMAs that
+      // completed (the producer waited for their slots), and on the normal
+      // path these waits return at once.
       volatile int no_abort = 0;
       for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
         mbar_wait(&full_bar[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, &no_abort);
@@ -340,7 +368,7 @@ __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(&full_bar[s], ph, &abort_flag)) break;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag, wait_ns)) break;
       tmem_fence_after();
       const uint64_t adesc = smem_desc_sw128(smA + s * S::A_BYTES);
       const uint64_t bdesc = smem_desc_sw128(smB + s * S::B_BYTES);

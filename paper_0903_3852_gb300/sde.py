@@ -117,6 +117,10 @@ SIGNATURES = [
      [ctypes.POINTER(JJPoint), ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
       ctypes.c_int64, ctypes.c_int64] + [_VP] * 9 + [_VP]),
     ("sde_box_muller_words", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP]),
+    ("sde_set_wait_limit", ctypes.c_int, [_VP, ctypes.c_uint64]),
+    ("sde_mlp_use_tensor_cores", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("sde_mlp_check", ctypes.c_int, [_VP]),
+    ("sde_debug_fail_allocation", None, [ctypes.c_int32]),
     ("sde_fp32_fma_probe", ctypes.c_int,
      [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     ("sde_josephson_run_fp64", ctypes.c_int,
@@ -301,6 +305,11 @@ class Ensemble:
         _check(lib().sde_last_kernel_stats(self._h, ctypes.byref(m), ctypes.byref(t), ctypes.byref(n)))
         return m.value, t.value, n.value
 
+    def set_wait_limit(self, ns):
+        """Limit (ns) of the bounded device waits of later launches; 0 = the
+        default one second."""
+        _check(lib().sde_set_wait_limit(self._h, ns))
+
     def close(self):
         if getattr(self, "_h", None):
             lib().sde_destroy(self._h)
@@ -392,6 +401,11 @@ def josephson_run_fp64(point, steps_per_period, total_steps, seed, n_begin, n_en
         _stream(stream)))
 
 
+def debug_fail_allocation(nth):
+    """sde_debug_fail_allocation: the nth allocation of the next create call fails."""
+    lib().sde_debug_fail_allocation(nth)
+
+
 def fp32_fma_probe(packed, iters, grid, block, sink, stream=None):
     """sde_fp32_fma_probe: launch the FP32 FMA throughput probe on `stream`;
     sink is a float32 CUDA tensor of at least grid * block elements.  Returns
@@ -461,6 +475,15 @@ class Mlp:
 
     def set_lr(self, lr):
         _check(lib().sde_mlp_set_lr(self._h, lr))
+
+    def use_tensor_cores(self, enable=True):
+        """Tensor-core forward (default where the shape allows it) or the CUDA-core one."""
+        _check(lib().sde_mlp_use_tensor_cores(self._h, 1 if enable else 0))
+
+    def check(self):
+        """Synchronise; raises SDEError (SDE_ERR_TIMEOUT) if a tensor-core forward
+        kernel reported an expired wait since the last check."""
+        _check(lib().sde_mlp_check(self._h))
 
     def train_step(self, X, y, loss=None, stream=None):
         _check(lib().sde_mlp_train_step(self._h, _ptr(X), _ptr(y), X.shape[0], _ptr(loss), _stream(stream)))

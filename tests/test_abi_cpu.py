@@ -75,7 +75,7 @@ int main(void) {
 
 
 def test_validation_before_any_cuda_call(L):
-    assert L.sde_abi_version() == 100
+    assert L.sde_abi_version() == 101
     h = ctypes.c_void_p()
     assert L.sde_create(None, ctypes.byref(h)) == 1
     assert b"cfg" in L.sde_last_error()
@@ -195,3 +195,29 @@ def test_noalloc_wrapper_checks_buffers_before_the_call():
     # right sizes and types, but host memory: refused before the C call
     with pytest.raises(ValueError, match="current CUDA device"):
         call()
+
+
+def test_injected_allocation_failure_reports_no_memory(L):
+    """sde_debug_fail_allocation(1) makes the next sde_create fail at its first
+    allocation, the host context, after validation and before any CUDA call:
+    SDE_ERR_NO_MEMORY and a NULL context; the injection is then disarmed."""
+    pts = (sde.JJPoint * 1)(sde.JJPoint(0.9, 4.2, 4.9, 0.1, 1e-3))
+    paths = (ctypes.c_int64 * 1)(64)
+    steps = (ctypes.c_int64 * 1)(100)
+    cfg = sde.Config()
+    cfg.model, cfg.schedule, cfg.n_points, cfg.steps_per_period = sde.SDE_JOSEPHSON, 0, 1, 200
+    cfg.points = ctypes.cast(pts, ctypes.POINTER(sde.JJPoint))
+    cfg.paths, cfg.steps = paths, steps
+    cfg.block_threads, cfg.paths_per_thread = 128, 1
+    h = ctypes.c_void_p(1)
+    L.sde_debug_fail_allocation(1)
+    assert L.sde_create(ctypes.byref(cfg), ctypes.byref(h)) == sde.SDE_ERR_NO_MEMORY
+    assert h.value is None
+    assert "allocation" in L.sde_last_error().decode()
+    # disarmed: the next call gets past the host allocation (without a GPU it
+    # then stops at the first CUDA call)
+    st = L.sde_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert st != sde.SDE_ERR_NO_MEMORY
+    if st == sde.SDE_OK:
+        L.sde_destroy(h)
+    assert L.sde_set_wait_limit(None, 5) == sde.SDE_ERR_INVALID_ARG
