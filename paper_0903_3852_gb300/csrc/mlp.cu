@@ -8,10 +8,14 @@
 // weights.  Every GEMM reads BF16 operands (weights and activations rounded
 // from FP32) and accumulates in FP32; pre-activations are kept in FP32.
 //
-// The GEMMs are small (batch x 256 x 256): one tiled kernel with 64 x 64
-// output tiles covers all three shapes (forward, weight gradient, input
-// gradient) through layout flags, with the bias / activation / derivative
-// fused into its epilogue.
+// Inference (sde_mlp_forward) of width-256 networks with at least two hidden
+// layers runs the fused tensor-core kernel of mlp_tc.cuh: the square hidden
+// layers as tcgen05 MMAs (M = 128 points, N = 256, K = 256) with the bias,
+// SiLU and the output layer in their epilogues.  The training path (forward
+// with stored pre-activations, backward, Adam) uses one tiled CUDA-core kernel
+// with 64 x 64 output tiles for all three GEMM shapes (forward, weight
+// gradient, input gradient) through layout flags, with the bias / activation /
+// derivative fused into its epilogue.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -22,7 +26,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "mlp_tc.cuh"
 #include "philox.cuh"
+#include "tma_map.h"
 
 using sde::cuda_fail;
 using sde::set_error;
@@ -227,6 +233,23 @@ __global__ void ensemble_stats_kernel(const float *out, int members, int64_t str
 
 int grid1(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
+// BF16 copies of the square hidden layers' weights for the tensor-core
+// forward: whh[member][l][n][k] = W_{l+1}[n][k] of that member.
+struct SquareOffsets {
+  int64_t w[mlptc::MAX_HH];
+};
+
+__global__ void square_weights_kernel(const float *params, int64_t P, int members, int n_hh, SquareOffsets off,
+                                      __nv_bfloat16 *whh) {
+  constexpr int64_t HH = (int64_t)mlptc::H * mlptc::H;
+  const int64_t n = (int64_t)members * n_hh * HH;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ml = i / HH;
+    const int member = (int)(ml / n_hh), l = (int)(ml % n_hh);
+    whh[i] = __float2bfloat16_rn(params[(int64_t)member * P + off.w[l] + (i - ml * HH)]);
+  }
+}
+
 }  // namespace
 }  // namespace sde
 
@@ -247,6 +270,12 @@ struct sde_mlp {
   int64_t *off_dev = nullptr;
   int *fin_dev = nullptr;
   int64_t step = 0;
+  // tensor-core forward (width 256, at least two hidden layers)
+  bool tc = false;                 // the shape has the tensor-core path
+  bool use_tc = true;              // sde_mlp_use_tensor_cores
+  __nv_bfloat16 *whh = nullptr;    // [members][n_hidden - 1][256][256]
+  CUtensorMap map_whh;
+  uint32_t *err = nullptr;         // latched kErrTimeout of the tensor-core kernel
 };
 
 namespace {
@@ -341,6 +370,8 @@ void mlp_free(sde_mlp *q) {
   cudaFree(q->lo_hi);
   cudaFree(q->off_dev);
   cudaFree(q->fin_dev);
+  cudaFree(q->whh);
+  cudaFree(q->err);
   delete q;
 }
 
@@ -388,7 +419,7 @@ sde_status sde_mlp_create(const sde_mlp_config *cfg, sde_mlp **out) {
   sde_status st = SDE_OK;
   auto alloc = [&](void **p, size_t bytes) {
     if (st != SDE_OK) return;
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    cudaError_t e = device_alloc(p, bytes ? bytes : 1);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
   };
   alloc((void **)&q->params, sizeof(float) * M * q->P);
@@ -408,6 +439,19 @@ sde_status sde_mlp_create(const sde_mlp_config *cfg, sde_mlp **out) {
   alloc((void **)&q->lo_hi, sizeof(float) * 10);
   alloc((void **)&q->off_dev, sizeof(int64_t) * (q->L + 1));
   alloc((void **)&q->fin_dev, sizeof(int) * q->L);
+  alloc((void **)&q->err, sizeof(uint32_t));
+  q->tc = cfg->hidden == mlptc::H && cfg->n_hidden >= 2 && cfg->n_hidden - 1 <= mlptc::MAX_HH &&
+          cfg->n_in <= mlptc::MAX_IN;
+  if (q->tc) alloc((void **)&q->whh, sizeof(__nv_bfloat16) * M * (cfg->n_hidden - 1) * H * H);
+  alloc_injection_disarm();
+  if (st == SDE_OK && q->tc) {
+    st = make_map_bf16(&q->map_whh, q->whh, M * (cfg->n_hidden - 1) * H, H, mlptc::H);
+    if (st == SDE_OK) {
+      const cudaError_t e = cudaFuncSetAttribute(mlptc::mlp_fwd_tc_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mlptc::SMEM_BYTES);
+      if (e != cudaSuccess) st = cuda_fail(e, "cudaFuncSetAttribute(mlp_fwd_tc_kernel)");
+    }
+  }
   if (st == SDE_OK) {
     float lh[10];
     for (int k = 0; k < 5; ++k) {
@@ -420,6 +464,7 @@ sde_status sde_mlp_create(const sde_mlp_config *cfg, sde_mlp **out) {
     if (e == cudaSuccess) e = cudaMemcpy(q->off_dev, offs.data(), sizeof(int64_t) * offs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(q->fin_dev, q->fin.data(), sizeof(int) * q->L, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(q->m, 0, sizeof(float) * M * q->P);
+    if (e == cudaSuccess) e = cudaMemset(q->err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(q->v, 0, sizeof(float) * M * q->P);
     for (int mm = 0; mm < M && e == cudaSuccess; ++mm) {
       init_kernel<<<grid1(q->P), 256>>>(q->params, q->off_dev, q->fin_dev, q->L, q->P, mm, cfg->seed);
@@ -478,9 +523,38 @@ sde_status sde_mlp_forward(sde_mlp *q, const float *X, int64_t B, float *mean, f
   if (B == 0) return SDE_OK;
   SDE_CHECK_ARG(X && mean, "X and mean must be non-NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int mm = 0; mm < q->cfg.n_members; ++mm) {
-    sde_status st = mlp_forward_member(q, mm, X, B, q->out + (int64_t)mm * q->cfg.max_batch, s);
-    if (st != SDE_OK) return st;
+  if (q->tc && q->use_tc) {
+    const int n_hh = q->cfg.n_hidden - 1;
+    SquareOffsets so{};
+    mlptc::Args a{};
+    for (int l = 0; l < n_hh; ++l) {
+      so.w[l] = q->woff[l + 1];
+      a.off_bh[l] = q->boff[l + 1];
+    }
+    square_weights_kernel<<<grid1((int64_t)q->cfg.n_members * n_hh * mlptc::H * mlptc::H), 256, 0, s>>>(
+        q->params, q->P, q->cfg.n_members, n_hh, so, q->whh);
+    SDE_CUDA_TRY(cudaGetLastError());
+    a.X = X;
+    a.params = q->params;
+    a.P = q->P;
+    a.B = B;
+    a.n_in = q->cfg.n_in;
+    a.n_hh = n_hh;
+    a.off_w0 = q->woff[0];
+    a.off_b0 = q->boff[0];
+    a.off_wo = q->woff[q->L - 1];
+    a.off_bo = q->boff[q->L - 1];
+    a.out = q->out;
+    a.out_stride = q->cfg.max_batch;
+    a.err = q->err;
+    const dim3 grid((unsigned)((B + mlptc::BM - 1) / mlptc::BM), (unsigned)q->cfg.n_members);
+    mlptc::mlp_fwd_tc_kernel<<<grid, mlptc::THREADS, mlptc::SMEM_BYTES, s>>>(q->map_whh, a);
+    SDE_CUDA_TRY(cudaGetLastError());
+  } else {
+    for (int mm = 0; mm < q->cfg.n_members; ++mm) {
+      sde_status st = mlp_forward_member(q, mm, X, B, q->out + (int64_t)mm * q->cfg.max_batch, s);
+      if (st != SDE_OK) return st;
+    }
   }
   ensemble_stats_kernel<<<grid1(B), 256, 0, s>>>(q->out, q->cfg.n_members, q->cfg.max_batch, B, mean, spread);
   SDE_CUDA_TRY(cudaGetLastError());
@@ -495,6 +569,31 @@ sde_status sde_mlp_grad(sde_mlp *q, int32_t member, const float *X, const float 
   SDE_CHECK_ARG(B >= 1 && B <= q->cfg.max_batch, "batch must be in [1, max_batch]");
   SDE_CHECK_ARG(X && y && grad, "X, y and grad must be non-NULL");
   return mlp_grad_member(q, member, X, y, B, grad, loss, (cudaStream_t)stream);
+}
+
+sde_status sde_mlp_use_tensor_cores(sde_mlp *q, int32_t enable) {
+  clear_error();
+  SDE_CHECK_ARG(q != nullptr, "mlp is NULL");
+  if (enable && !q->tc) {
+    set_error("the tensor-core forward needs hidden == 256, 2..8 hidden layers and n_in <= 8");
+    return SDE_ERR_UNSUPPORTED;
+  }
+  q->use_tc = enable != 0;
+  return SDE_OK;
+}
+
+sde_status sde_mlp_check(sde_mlp *q) {
+  clear_error();
+  SDE_CHECK_ARG(q != nullptr, "mlp is NULL");
+  SDE_CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t err = 0;
+  SDE_CUDA_TRY(cudaMemcpy(&err, q->err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (err) SDE_CUDA_TRY(cudaMemset(q->err, 0, sizeof(uint32_t)));
+  if (err & kErrTimeout) {
+    set_error("a bounded device wait of the tensor-core forward expired");
+    return SDE_ERR_TIMEOUT;
+  }
+  return SDE_OK;
 }
 
 sde_status sde_mlp_set_lr(sde_mlp *q, float lr) {

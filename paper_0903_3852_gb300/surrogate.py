@@ -6,11 +6,14 @@ Pipeline, all compute in the CUDA library:
    one persistent sweep launch (the engine of the batched Josephson sweep).
 2. ``Surrogate.fit``: an ensemble of networks (5 -> 256 x 3 -> 1, SiLU) trained
    by the library's BF16 forward/backward/Adam kernels on simulated labels.
-3. ``Surrogate.calibrate``: the ensemble spread times a factor k, chosen on
-   held-out calibration points so that |prediction - label| <= k spread for a
-   given share of them, is the predicted error.
+3. ``Surrogate.calibrate``: selective calibration on held-out points.  The
+   network is trusted below a spread threshold tau, the largest for which the
+   calibration points with spread <= tau miss the tolerance (beyond their own
+   labels' noise) at a rate of at most `risk`, counted conservatively
+   ((misses + 1) / (points + 1)); the predicted error is tol * spread / tau.
 4. ``Surrogate.answer``: network prediction where the predicted error is at
-   most the tolerance, the simulator's own <<v>> elsewhere (fallback).
+   most the tolerance, the simulator's own <<v>> elsewhere (fallback; also
+   wherever the prediction is not finite).
 
 The per-point arithmetic (features, the networks and their spread, the
 simulations) runs in the CUDA library; this module batches and shuffles, and
@@ -52,11 +55,11 @@ def simulate(points, paths, steps, seed, stream=None, init_seed=None):
 
 
 class Surrogate:
-    def __init__(self, members=4, max_batch=16384, lr=1e-3, seed=0):
+    def __init__(self, members=4, max_batch=131072, lr=1e-3, seed=0):
         self.mlp = sde.Mlp(members=members, max_batch=max_batch, lr=lr, seed=seed)
         self.max_batch = max_batch
         self.lr = lr
-        self.k = None
+        self.tau = None
 
     def features(self, points):
         return self.mlp.features(sde.points_to_device(points))
@@ -95,33 +98,40 @@ class Surrogate:
             spreads.append(s)
         return torch.cat(means).cpu().numpy(), torch.cat(spreads).cpu().numpy()
 
-    def calibrate(self, points, y, coverage=0.95, bins=8):
-        """Factors k with |prediction - y| <= k spread on `coverage` of the
-        calibration points, one per bin of spread (quantile bins), so that the
-        predicted error k(spread) spread adapts to regions where the spread is
-        more or less faithful.  Returns the overall factor."""
+    def calibrate(self, points, y, se, tol, risk=5e-4):
+        """Spread threshold tau on held-out calibration points with labels y of
+        standard error se: a point counts as a miss when |prediction - y| >
+        tol + 3 se, i.e. when the label rules out an error within tol (the
+        acceptance rule of the evaluation, against its own reference); tau is
+        the largest spread at which the points with spread <= tau have
+        (misses + 1) / (points + 1) <= risk.  Returns (tau, share of the
+        calibration points answered)."""
         mean, spread = self.predict(points)
-        ratio = np.abs(mean - np.asarray(y)) / np.maximum(spread, 1e-12)
-        self.edges = np.quantile(spread, np.linspace(0, 1, bins + 1)[1:-1])
-        which = np.searchsorted(self.edges, spread)
-        self.kbin = np.array([np.quantile(ratio[which == b], coverage) if np.any(which == b)
-                              else np.quantile(ratio, coverage) for b in range(bins)])
-        self.k = float(np.quantile(ratio, coverage))
-        return self.k
+        y, se = np.asarray(y, dtype=np.float64), np.asarray(se, dtype=np.float64)
+        miss = ~(np.abs(mean - y) <= tol + 3.0 * se)  # NaN counts as a miss
+        order = np.argsort(spread, kind="stable")
+        misses = np.cumsum(miss[order])
+        count = np.arange(1, len(order) + 1)
+        ok = (misses + 1.0) / (count + 1.0) <= risk
+        self.tau = float(spread[order][np.flatnonzero(ok)[-1]]) if ok.any() else 0.0
+        self.tol = tol
+        return self.tau, float(np.mean(spread <= self.tau)) if self.tau > 0 else 0.0
 
     def predicted_error(self, spread):
-        return self.kbin[np.searchsorted(self.edges, spread)] * spread
+        if self.tau <= 0.0:
+            return np.full(np.shape(spread), np.inf)
+        return self.tol * np.asarray(spread, dtype=np.float64) / self.tau
 
     def answer(self, points, tol, fallback_paths, steps, seed):
         """Network prediction where its predicted error is <= tol, simulator elsewhere.
         Returns dict(value, predicted_error, fallback mask, seconds split)."""
-        assert self.k is not None, "calibrate first"
+        assert self.tau is not None, "calibrate first"
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mean, spread = self.predict(points)
         t_mlp = time.perf_counter() - t0
         perr = self.predicted_error(spread)
-        fb = perr > tol
+        fb = ~(perr <= tol) | ~np.isfinite(mean)
         value = mean.astype(np.float64).copy()
         t_sim = 0.0
         if fb.any():

@@ -148,3 +148,63 @@ def test_training_converges_on_smooth_target():
     mse = float(((mean - yd) ** 2).mean())
     print("train mse %.3e (target variance %.3e)" % (mse, float(yd.var())))
     assert mse < 0.02 * float(yd.var())
+
+
+@pytest.mark.parametrize("B", [1, 127, 300, 1029])
+def test_tensor_core_forward_against_cuda_core_and_fp64(B):
+    """The fused tcgen05 forward (square layers on the tensor cores, 128-point
+    tiles, ragged last tile) against the CUDA-core forward of the same
+    parameters and against the FP64 reference network, for 4 members with
+    different weights.  Both GPU forms round the same operands to BF16; they
+    differ in summation order and in the SiLU evaluation, so an activation can
+    round to the neighbouring BF16 value: the outputs agree to ~1e-3 of the
+    output scale, and each is within the BF16 error of the FP64 network."""
+    rng = np.random.default_rng(B)
+    X = rng.uniform(-1, 1, (B, 5))
+    m = _mlp(members=4, max_batch=2048, seed=11)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    mean_tc, spread_tc = m.forward(Xd)
+    m.check()
+    m.use_tensor_cores(False)
+    mean_cc, spread_cc = m.forward(Xd)
+    m.use_tensor_cores(True)
+    outs = []
+    for q in range(4):
+        p = _unflat(m.get_params(q).cpu().numpy().astype(np.float64))
+        outs.append(ref.forward(p, X.astype(np.float32).astype(np.float64))[0])
+    outs = np.array(outs)
+    scale = max(1.0, np.abs(outs).max())
+    a, b = mean_tc.cpu().numpy().astype(np.float64), mean_cc.cpu().numpy().astype(np.float64)
+    print("B=%d: |tc - cuda-core| max %.2e, |tc - fp64| max %.2e, |cc - fp64| max %.2e (scale %.2f)"
+          % (B, np.abs(a - b).max(), np.abs(a - outs.mean(0)).max(), np.abs(b - outs.mean(0)).max(), scale))
+    assert np.all(np.isfinite(a))
+    assert np.abs(a - b).max() <= 2e-3 * scale
+    assert np.abs(a - outs.mean(0)).max() <= 1e-2 * scale
+    sp_tc, sp_cc = spread_tc.cpu().numpy(), spread_cc.cpu().numpy()
+    assert np.abs(sp_tc - sp_cc).max() <= 2e-3 * scale
+
+
+def test_tensor_core_forward_after_training_and_selection():
+    """After a few hundred Adam steps (trained weights, not just the initial
+    ones) the tensor-core forward still matches the CUDA-core forward; a shape
+    without the tensor-core path refuses it."""
+    rng = np.random.default_rng(5)
+    n = 2048
+    X = rng.uniform(-1, 1, (n, 5)).astype(np.float32)
+    y = (np.sin(3 * X[:, 0]) * X[:, 1] + X[:, 2] ** 2).astype(np.float32)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    m = _mlp(members=2, max_batch=n, lr=2e-3, seed=2)
+    for step in range(300):
+        idx = torch.from_numpy(rng.integers(0, n, 256)).cuda()
+        m.train_step(Xd[idx].contiguous(), yd[idx].contiguous())
+    a, _ = m.forward(Xd)
+    m.use_tensor_cores(False)
+    b, _ = m.forward(Xd)
+    m.check()
+    d = (a - b).abs().max().item()
+    print("trained: |tc - cuda-core| max %.2e, target scale %.2f" % (d, float(yd.abs().max())))
+    assert d <= 2e-3 * max(1.0, float(yd.abs().max()))
+    small = _mlp(members=1, max_batch=64, hidden=128)
+    with pytest.raises(sde.SDEError) as e:
+        small.use_tensor_cores(True)
+    assert e.value.status == sde.SDE_ERR_UNSUPPORTED
