@@ -33,6 +33,13 @@ from paper_0903_3852_gb300 import dist as sde_dist  # noqa: E402
 from paper_0903_3852_gb300 import inputs  # noqa: E402
 
 PAPER_FLOP_PER_STEP = 79  # Table 1 (Appendix): FLOP per SRK2 step of Eq. 1, weighted
+# FP32 operations per SRK2 path-step of the Josephson kernels as the hardware
+# counts them (ncu: 2 x FFMA + FADD + FMUL, the packed FP32x2 forms counting
+# both lanes): the same arithmetic in every launch variant.  The paper's
+# weighting above counts each transcendental as several FLOP; these kernels
+# take them from tables and polynomials, so the counted figure is the
+# roofline's numerator and the weighted one is reported beside it.
+COUNTED_FLOP_PER_PATH_STEP = 52.27
 PAPER_FLOP_MEANFIELD = 66  # Fig. 5: operations per step of PROG3 (Eq. 3, mean field)
 PAPER_FLOP_PAIR = 6  # Fig. 5: 44 + 6N operations per step of PROG2, 6 per pair term
 L2_FLUSH_BYTES = 256 << 20
@@ -46,7 +53,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep",
                     choices=["sweep", "plain", "kuramoto-meanfield", "kuramoto-pairwise",
-                             "kuramoto-general", "kuramoto-general-fp32", "surrogate", "fig2",
+                             "kuramoto-general", "kuramoto-general-fp32", "surrogate", "surrogate-inference", "fig2",
                              "kuramoto-fig4", "fig2-fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pairwise-steps", type=int, default=200,
@@ -75,6 +82,8 @@ def parse():
                     help="fixed Josephson launch variant, skipping the autotuner: 1, 2 or 4 paths per "
                          "thread, 11 / 12 / 14 the same with fewer registers")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="sweep: skip the plain per-path kernel comparison of the default line")
     ap.add_argument("--fused", action="store_true",
                     help="general coupling, tensor-core form: SRK2 sub-steps in the GEMM epilogue")
     return ap.parse_args()
@@ -203,6 +212,57 @@ def fp32_peak_tflops(props):
     # 128 FP32 lanes per SM on Blackwell, one FMA (2 FLOP) per lane per clock,
     # at the maximum SM clock of 2070 MHz.
     return props.multi_processor_count * 128 * 2 * 2.070e9 / 1e12
+
+
+def measure_fp32_peak(device, launches=6, target_ms=60.0):
+    """The FP32 peak measured on this GPU: the library's FMA probe (eight
+    independent FFMA2 chains per thread, 8 blocks of 256 threads per SM),
+    timed with CUDA events on the launching stream; best launch, with the SM
+    clock sampled meanwhile."""
+    import torch
+    from paper_0903_3852_gb300 import sde
+    props = torch.cuda.get_device_properties(device)
+    grid, block = props.multi_processor_count * 8, 256
+    sink = torch.empty(grid * block, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def one(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flop = sde.fp32_fma_probe(1, iters, grid, block, sink, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return flop, e0.elapsed_time(e1)
+
+    iters = 1024
+    for _ in range(2):
+        _, t = one(iters)
+        iters = max(1, int(iters * target_ms / max(t, 1e-3)))
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.3)
+    best = 0.0
+    for _ in range(launches):
+        flop, t = one(iters)
+        best = max(best, flop / (t * 1e-3) / 1e12)
+    clk = clocks.stop()
+    return {"tflops": best, "sm_mhz": clk.get("sm_mhz"), "reasons": clk.get("reasons"),
+            "derived_2070mhz": fp32_peak_tflops(props),
+            "probe": "FFMA2 chains, %d blocks x %d threads, best of %d launches of ~%.0f ms"
+                     % (grid, block, launches, target_ms)}
+
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_ours(args, rank, world, device):
@@ -461,6 +521,7 @@ def run_ours(args, rank, world, device):
                          "paper_seconds_c1060_fp32": 20.0}
     k_ms = statistics.mean(kernel_ms)
     peaks, peak_src = measured_peaks()
+    fp32 = measure_fp32_peak(device)
     if args.workload == "kuramoto-fig4":
         bound, peak = "hbm", peaks["hbm_gbs"]
         peak_note = "HBM copy bandwidth, %s" % peak_src
@@ -474,34 +535,41 @@ def run_ours(args, rank, world, device):
         peak_note = "bf16 dense, sustained, %s" % peak_src
         flop_note = "2 N (2R) N FLOP per GEMM launch"
     else:
-        bound, peak = "alu", fp32_peak_tflops(props)
-        peak_note = "%d SM x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)" % props.multi_processor_count
+        bound, peak = "alu", fp32["tflops"]
+        peak_note = ("FP32 FMA probe measured in this run (%.1f TFLOP/s at %s MHz; %.1f derived from 128 "
+                     "lanes x 2 FLOP x 2070 MHz)" % (fp32["tflops"], fp32["sm_mhz"], fp32["derived_2070mhz"]))
         flop_note = ("2 N (2R) N FLOP per GEMM launch (FP32 FMA)" if args.workload == "kuramoto-general-fp32"
                      else "%d FLOP per unit (paper Table 1 weighting)" % flop_per_unit)
+    counted = args.workload in ("sweep", "plain", "fig2") and not args.euler
     if args.workload in ("sweep", "plain", "fig2"):
+        if counted:
+            flop_per_unit = COUNTED_FLOP_PER_PATH_STEP
+            flop_note = ("%.2f FP32 FLOP per path-step counted by ncu (2 x FFMA + FADD + FMUL, packed "
+                         "instructions both lanes)" % flop_per_unit)
         flop_per_launch = flop_per_unit * units / launches_kernel
     if args.workload == "kuramoto-fig4":
         achieved = bytes_per_launch / (k_ms * 1e-3) / 1e9
     else:
         achieved = flop_per_launch / (k_ms * 1e-3) / 1e12
-    # DRAM bytes per launch of the dominant kernel from the ncu captures
-    # summarised under profiles/ (null where the kernel changed since)
+    # DRAM bytes per launch of the dominant kernel, dram__bytes_read.sum +
+    # dram__bytes_write.sum of one ncu capture of that kernel (scaled by the
+    # units where the capture was smaller); null where the kernel changed since
     traffic, traffic_src = None, None
     if args.workload in ("sweep", "plain", "fig2") and not args.euler:
-        traffic = 8.23 * n  # jj_kernel: 8.23 B per path (the initial state read once)
-        traffic_src = "profiles/jj_kernel_sweep_512pts_cap2000.md, scaled by paths"
+        traffic = 8.23 * n  # 8.23 B per path: the initial state read once
+        traffic_src = "ncu capture of the sweep kernel (2000-step cap), scaled by paths"
     elif args.workload == "kuramoto-fig4":
         traffic = 16.6 * w["n_osc"] * w["replicas"]  # mean over the launches of 4 steps
-        traffic_src = "profiles/kur_mfg_kernel_fig4_N16777216.md"
+        traffic_src = "ncu capture of the grid-wide mean-field launches"
     elif args.workload == "kuramoto-general" and not args.fused:
-        traffic = 146.2e6  # tc_gemm_bf16_kernel: K (134 MB) once + operands and output
-        traffic_src = "profiles/tc_gemm_bf16_kernel_N8192_R256.md"
+        traffic = 146.2e6  # K (134 MB) once + operands and output
+        traffic_src = "ncu capture of the tensor-core GEMM"
     elif args.workload == "kuramoto-meanfield":
         traffic = 2.43e6  # phases and omega read once per run; results stay in L2
-        traffic_src = "profiles/kur_meanfield_cluster_kernel_N4096_R64.md"
+        traffic_src = "ncu capture of the cluster mean-field kernel"
     elif args.workload == "kuramoto-pairwise" and not args.euler:
         traffic = 2.11e6
-        traffic_src = "profiles/kur_pairwise_stage_N4096_R64.md"
+        traffic_src = "ncu capture of the pairwise stage kernel"
     res = {
         "metric": metric,
         "value": sde_dist.aggregate_rate(units, world, ms * 1e-3),
@@ -520,15 +588,62 @@ def run_ours(args, rank, world, device):
                      "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "flop_model": flop_note,
-                     "peak_source": peak_note, "kernel_ms_per_launch": k_ms},
+                     "peak_source": peak_note, "kernel_ms_per_launch": k_ms,
+                     "fp32_peak_probe": fp32},
         "e2e": {"value": units * world / (e2e * 1e-3) if e2e else None, "unit": metric.split("/")[0] + "/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "wall_s_timed": t_wall,
     }
+    if counted:
+        res["roofline"]["frac_paper_weighted_79flop"] = (PAPER_FLOP_PER_STEP * units / launches_kernel
+                                                         / (k_ms * 1e-3) / 1e12 / peak)
+    if args.workload == "sweep" and not args.euler and not args.no_plain and world == 1 and sched != sde.SDE_SCHED_PLAIN:
+        res["plain_vs_batched"] = plain_comparison(args, device, res["value"], fp32["tflops"])
     res.update(extra)
     return res, ens
+
+
+def plain_comparison(args, device, batched_rate, peak):
+    """The plain per-path kernel (one thread per path, scalar FP32: Alg. 1 as
+    the paper writes it) against the batched form, at the same accuracy (the
+    same arithmetic: every launch variant gives the same bits): (a) at a size
+    that fills the GPU, the Fig. 2 ensemble of 2^19 paths in one launch, 2e4
+    of its 2e5 steps; (b) on the sweep itself, one plain launch per point."""
+    import torch
+    from paper_0903_3852_gb300 import sde
+    out = {}
+    cases = [("saturating", fig2_workload(0), 20_000), ("per_point_sweep", sweep_workload(0, args), None)]
+    for name, w, cap in cases:
+        if cap:
+            w["steps"] = np.minimum(w["steps"], cap)
+        ens = sde.Ensemble.josephson(w["points"], w["paths"], w["steps"], w["seed"],
+                                     steps_per_period=w["steps_per_period"], schedule=sde.SDE_SCHED_PLAIN,
+                                     paths_per_thread=1)
+        n = int(w["paths"].sum())
+        units = float((w["paths"] * w["steps"]).sum())
+        n_end = int(w["steps"].max())
+        x = torch.from_numpy(w["x0"]).to(device)
+        v = torch.from_numpy(w["v0"]).to(device)
+        xo, vo = torch.empty_like(x), torch.empty_like(v)
+        wo = torch.empty(n, dtype=torch.int32, device=device)
+        so = torch.empty(n, dtype=torch.float64, device=device)
+        ens.run_josephson(0, n_end, x, v, xo, vo, wo, so)  # warm-up
+        ms = []
+        for _ in range(2):
+            ens.run_josephson(0, n_end, x, v, xo, vo, wo, so)
+            ms.append(ens.last_kernel_ms())
+        t = min(ms) * 1e-3
+        rate = units / t
+        out[name] = {"workload": josephson_workload_name(args, w) if name == "per_point_sweep"
+                     else "josephson_fig2_%dpaths_%dsteps" % (n, n_end),
+                     "kernel": "one thread per path, scalar FP32", "launches": len(w["points"]),
+                     "tuning_block_threads": ens.tuning()[0], "path_steps": units, "value": rate,
+                     "unit": "path-steps/s", "frac": COUNTED_FLOP_PER_PATH_STEP * rate / 1e12 / peak,
+                     "batched_over_plain": batched_rate / rate}
+        ens.close()
+    return out
 
 
 # The paper's own figures for the exact workloads it timed (NVIDIA Tesla C1060,
@@ -766,9 +881,106 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; inputs.py)",
            "config": reference_config(args, last["sample"]),
            "cpu_baseline": {"value": v, "unit": unit, "cores": last["cores"], "kind": "oracle",
-                            "sample": last["sample"], "single_core": one},
+                            "sample": last["sample"], "single_core": one, "cpu_model": host_cpu_model()},
            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return res
+
+
+def surrogate_inference(sur, points, device, batch=100_000, reps=20):
+    """Inference throughput of the surrogate's ensemble at a batch of 10^5 points:
+    the fused tensor-core forward and the CUDA-core forward, each timed with CUDA
+    events on the launching stream over `reps` calls after 3 warm-ups; the
+    tensor-pipe fraction counts the square layers' MACs (2 x 256 x 256 per point,
+    layer and member) against the measured BF16 peak."""
+    import torch
+    stream = torch.cuda.current_stream()
+    X = sur.features(points[:batch])
+    B = X.shape[0]
+    mlp = sur.mlp
+    n_sq = mlp.cfg.n_hidden - 1
+    flop_tc = 2.0 * 256 * 256 * n_sq * mlp.members * B
+    peaks, src = measured_peaks()
+    out = {"batch": B, "members": mlp.members}
+    for name, tc in (("tensor_cores", True), ("cuda_cores", False)):
+        mlp.use_tensor_cores(tc)
+        for _ in range(3):
+            mlp.forward(X)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            mlp.forward(X)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_batch": ms, "points_per_sec": B / (ms * 1e-3),
+                     "square_layer_tflops": flop_tc / (ms * 1e-3) / 1e12}
+    mlp.use_tensor_cores(True)
+    mlp.check()
+    tf = out["tensor_cores"]["square_layer_tflops"]
+    out["tensor_pipe_frac"] = tf / peaks["bf16_tflops"]
+    out["tensor_pipe_peak"] = "bf16 dense burst, %s (%.0f TFLOP/s)" % (src, peaks["bf16_tflops"])
+    out["tensor_over_cuda_cores"] = out["cuda_cores"]["ms_per_batch"] / out["tensor_cores"]["ms_per_batch"]
+    return out
+
+
+def run_surrogate_inference(args, device):
+    """Inference of the surrogate's ensemble (4 networks 5-256-256-256-1) at a
+    batch of 10^5 parameter points: one bench step = one forward of the whole
+    batch through the library's fused tensor-core kernel (features in HBM).
+    The weights are the networks' seeded initial ones (the cost does not
+    depend on their values)."""
+    import torch
+    from paper_0903_3852_gb300 import build as sde_build
+    from paper_0903_3852_gb300 import surrogate
+
+    sde_build.build()
+    B = 100_000
+    sur = surrogate.Surrogate(members=4, max_batch=131072, seed=3)
+    pts = inputs.surrogate_points(B, seed=6)
+    X = sur.features(pts)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    for _ in range(max(args.warmup, 0)):
+        sur.mlp.forward(X)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device)
+    clocks.start()
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sur.mlp.forward(X)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    sur.mlp.check()
+    # end to end: features from host parameter points, the forward, the
+    # mean and spread back to the host
+    e2e = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sur.predict(pts)
+        e2e.append(time.perf_counter() - t0)
+    t = statistics.mean(ms) * 1e-3
+    flop = 2.0 * 256 * 256 * 2 * 4 * B
+    peaks, src = measured_peaks()
+    return {
+        "metric": "points/sec", "value": B / t, "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 operands, fp32 accumulation", "data": "synthetic (seeded; inputs.py)",
+        "config": {"workload": "surrogate_inference_batch100000", "members": 4, "net": "5-256-256-256-1 SiLU",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "roofline": {"bound": "tensor", "achieved": flop / t / 1e12, "peak": peaks["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": flop / t / 1e12 / peaks["bf16_tflops"], "traffic": None,
+                     "flop_model": "2 x 256 x 256 FLOP per point, square layer and member (the tensor-core work)",
+                     "peak_source": "bf16 dense burst, %s" % src, "kernel_ms_per_launch": t * 1e3},
+        "e2e": {"value": B / statistics.median(e2e), "unit": "points/s", "h2d_bytes_per_step": 40 * B,
+                "d2h_bytes_per_step": 8 * B},
+        "gpu_launches": 3 * args.steps, "clocks": clk,
+    }
 
 
 def run_surrogate(args, device):
@@ -786,24 +998,16 @@ def run_surrogate(args, device):
     train = inputs.surrogate_points(100_000, seed=6)
     y, se, t_lab = surrogate.simulate(train, 2048, steps, seed=6)
     label_units = len(train) * 2048.0 * steps
-    sur = surrogate.Surrogate(members=4, max_batch=16384, lr=2e-3, seed=3)
+    sur = surrogate.Surrogate(members=4, max_batch=131072, lr=2e-3, seed=3)
     t0 = time.perf_counter()
     sur.fit(train[:90_000], y[:90_000], epochs=120, batch=1024)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
-    sur.calibrate(train[90_000:], y[90_000:])
+    tau, cal_share = sur.calibrate(train[90_000:], y[90_000:], se[90_000:], tol, risk=5e-4)
     evalp = inputs.surrogate_points(10_000, seed=7)
     ref, ref_se, t_ref = surrogate.simulate(evalp, 8192, steps, seed=7)
-    # inference throughput at batch 10^4 (features + 4 networks + spread)
-    X = sur.features(evalp)
-    for _ in range(3):
-        sur.mlp.forward(X)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(10):
-        sur.mlp.forward(X)
-    torch.cuda.synchronize()
-    mlp_pps = 10 * len(evalp) / (time.perf_counter() - t0)
+    infer = surrogate_inference(sur, train, device)
+    mlp_pps = infer["tensor_cores"]["points_per_sec"]
     for _ in range(max(args.warmup, 0)):
         out = sur.answer(evalp, tol, 8192, steps, seed=8)
     clocks = ClockSampler(device)
@@ -823,7 +1027,7 @@ def run_surrogate(args, device):
     fb_units = float(out["fallback"].sum()) * 8192.0 * steps
     k_ms = statistics.mean(kms)
     achieved = PAPER_FLOP_PER_STEP * fb_units / (k_ms * 1e-3) / 1e12
-    peak = fp32_peak_tflops(props)
+    peak = measure_fp32_peak(device)["tflops"]
     return {
         "metric": "points/sec", "value": len(evalp) / t_step, "unit": "points/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
@@ -834,7 +1038,9 @@ def run_surrogate(args, device):
                    "net": "5-256-256-256-1 SiLU"},
         "surrogate": {"label_seconds": t_lab, "label_points_per_sec_2048_paths": len(train) / t_lab,
                       "label_path_steps_per_sec": label_units / t_lab, "fit_seconds": t_fit,
-                      "mlp_points_per_sec": mlp_pps,
+                      "mlp_points_per_sec": mlp_pps, "inference_batch_1e5": infer,
+                      "calibration": {"spread_threshold": tau, "answered_share": cal_share, "risk": 5e-4,
+                                      "points": 10_000},
                       "simulator_points_per_sec_8192_paths": len(evalp) / t_ref,
                       "answered_by_network": float(ans.mean()),
                       "within_tol_all": float(ok.mean()),
@@ -869,6 +1075,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "surrogate-inference":
+        res = run_surrogate_inference(args, local)
+        if rank == 0:
+            print(json.dumps(res))
+        return
     if args.workload == "surrogate":
         res = run_surrogate(args, local)
         if rank == 0:
@@ -878,6 +1089,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:  # the oracle baseline is a 1-GPU figure
             res["cpu_baseline"] = cpu_baseline_both(args)
+            res["cpu_baseline"]["cpu_model"] = host_cpu_model()
         print(json.dumps(res))
     ens.close()
     if world > 1:

@@ -198,7 +198,7 @@ __device__ __forceinline__ void jj_transform(const uint4 (&r)[ILP], const float 
 // of step n0 (n0 mod P) and is updated.
 // SCALED: `drive` holds a cos(2 pi k / P) + f for this point (a per-warp or
 // per-point table), else cos(2 pi k / P) and the drive term is formed here.
-template <int ILP, bool ACC, bool EM = false, bool SCALED = false>
+template <int ILP, bool ACC, bool EM = false, bool SCALED = false, bool ONEBB = false>
 __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float (&v)[ILP],
                                            double (&vs)[ILP], const JJConsts &c,
                                            const float *__restrict__ drive, int P, int &k,
@@ -218,7 +218,7 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
   // drawn while group g is stepped, in one basic block, so the integer Philox
   // work interleaves with the FP32 steps (16 more live registers; with fewer
   // paths per thread the lost occupancy costs more than the overlap gains).
-  constexpr bool PIPE = ILP >= 4;
+  constexpr bool PIPE = ILP >= 4;  // with ONEBB (the four-path kernels): see the group loop
   float z[ILP][4];
   if constexpr (PIPE) {
     uint4 r0[ILP];
@@ -229,6 +229,36 @@ __device__ __forceinline__ void jj_segment(float (&x)[ILP], int (&w)[ILP], float
   for (uint32_t gb = g0; gb <= g1; gb = (gb | 15u) + 1u) {
     const uint32_t ge = (gb | 15u) < g1 ? (gb | 15u) : g1;
     for (uint32_t g = gb; g <= ge; ++g) {
+      if constexpr (PIPE && ONEBB) {
+        // ONEBB: a whole group with P a multiple of 4 as one basic block --
+        // the next group's Philox words, the four steps, the position fold
+        // and the next group's Box-Muller transform -- so that the compiler
+        // can interleave the integer, special-function and FP32 work of
+        // all three (the same operations as below, in the same order per
+        // value: bit-identical).
+        const int64_t base = (int64_t)g << 2;
+        if ((P & 3) == 0 && base >= n0 && base + 4 <= n1) {
+          uint4 rn[ILP];
+#pragma unroll
+          for (int i = 0; i < ILP; ++i)
+            rn[i] = philox4x32_10(make_uint4(g + 1, pid[i], point, kTagJosephson), key);
+          const float4 d = *reinterpret_cast<const float4 *>(drive + k);
+          const float d4 = drive[k + 4];
+          float e[5];
+          e[0] = SCALED ? d.x : fmaf(c.a, d.x, c.f);
+          e[1] = SCALED ? d.y : fmaf(c.a, d.y, c.f);
+          e[2] = SCALED ? d.z : fmaf(c.a, d.z, c.f);
+          e[3] = SCALED ? d.w : fmaf(c.a, d.w, c.f);
+          e[4] = SCALED ? d4 : fmaf(c.a, d4, c.f);
+          k = (k + 4 == P) ? 0 : k + 4;
+#pragma unroll
+          for (int s = 0; s < 4; ++s) jj_steps<ILP, ACC, EM>(x, v, acc, z, s, c, e[s], e[s + 1]);
+#pragma unroll
+          for (int i = 0; i < ILP; ++i) jj_wrap(x[i], w[i]);
+          jj_transform<ILP>(rn, bm_tab, z);
+          continue;
+        }
+      }
       // PIPE: the Philox words of group g + 1 now, their Box-Muller
       // transform into z once this group's steps have read it
       uint4 rn[ILP];
@@ -297,7 +327,7 @@ __device__ __forceinline__ double warp_sum(double a) {
   return a;
 }
 
-template <int ILP, bool EM>
+template <int ILP, bool EM, bool ONEBB = false>
 __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const float *drive, float *wtab,
                                         const float *bm_tab, int lane) {
   const JJUnit un = A.units[u];
@@ -339,13 +369,16 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
       // this warp's copy of the drive term a cos(2 pi k / P) + f of the unit's point
       for (int q = lane; q < A.P + 4; q += 32) wtab[q] = fmaf(c.a, drive[q], c.f);
       __syncwarp();
-      jj_segment<ILP, false, EM, true>(x, w, v, vs, c, wtab, A.P, k, nb, split, key, pid, (uint32_t)un.point,
-                                       bm_tab);
-      jj_segment<ILP, true, EM, true>(x, w, v, vs, c, wtab, A.P, k, w0, ne, key, pid, (uint32_t)un.point, bm_tab);
+      jj_segment<ILP, false, EM, true, ONEBB>(x, w, v, vs, c, wtab, A.P, k, nb, split, key, pid,
+                                              (uint32_t)un.point, bm_tab);
+      jj_segment<ILP, true, EM, true, ONEBB>(x, w, v, vs, c, wtab, A.P, k, w0, ne, key, pid, (uint32_t)un.point,
+                                             bm_tab);
       __syncwarp();  // the table is rewritten for the warp's next unit
     } else {
-      jj_segment<ILP, false, EM>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid, (uint32_t)un.point, bm_tab);
-      jj_segment<ILP, true, EM>(x, w, v, vs, c, drive, A.P, k, w0, ne, key, pid, (uint32_t)un.point, bm_tab);
+      jj_segment<ILP, false, EM, false, ONEBB>(x, w, v, vs, c, drive, A.P, k, nb, split, key, pid,
+                                               (uint32_t)un.point, bm_tab);
+      jj_segment<ILP, true, EM, false, ONEBB>(x, w, v, vs, c, drive, A.P, k, w0, ne, key, pid, (uint32_t)un.point,
+                                              bm_tab);
     }
   }
   bool bad = false;
@@ -389,7 +422,7 @@ __device__ __forceinline__ void jj_unit(const JJLaunchArgs &A, int u, const floa
   if (lane == 0) A.partials[u] = Moments{cnt, mean, m2};
 }
 
-template <int ILP, bool EM>
+template <int ILP, bool EM, bool ONEBB = false>
 __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
   // drive table cos(2 pi k / P), k = 0 .. P + 3 (four entries of padding
   // repeat the start of the period), 16-byte aligned
@@ -411,11 +444,11 @@ __device__ __forceinline__ void jj_kernel_body(const JJLaunchArgs &A) {
       if (lane == 0) u = (int)atomicAdd(A.queue, 1u) + A.unit_begin;
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= A.unit_end) break;
-      jj_unit<ILP, EM>(A, u, drive_s, wtab, bm_tab, lane);
+      jj_unit<ILP, EM, ONEBB>(A, u, drive_s, wtab, bm_tab, lane);
     }
   } else {
     const int u = A.unit_begin + blockIdx.x * warps + (threadIdx.x >> 5);
-    if (u < A.unit_end) jj_unit<ILP, EM>(A, u, drive_s, wtab, bm_tab, lane);
+    if (u < A.unit_end) jj_unit<ILP, EM, ONEBB>(A, u, drive_s, wtab, bm_tab, lane);
   }
 }
 
@@ -438,7 +471,7 @@ __global__ void __launch_bounds__(512, 2) jj_kernel_cap64(const JJLaunchArgs A) 
 // warps, each with two independent pairs and the Philox work to overlap).
 template <int ILP, bool EM = false>
 __global__ void __maxnreg__(ILP == 2 ? 72 : 128) jj_kernel_packed(const JJLaunchArgs A) {
-  jj_kernel_body<ILP, EM>(A);
+  jj_kernel_body<ILP, EM, ILP >= 4>(A);
 }
 
 // Four paths per thread held to 96 registers (20 warps per SM in blocks of
@@ -446,7 +479,7 @@ __global__ void __maxnreg__(ILP == 2 ? 72 : 128) jj_kernel_packed(const JJLaunch
 // to overlap.
 template <bool EM = false>
 __global__ void __maxnreg__(96) jj_kernel_packed4_cap96(const JJLaunchArgs A) {
-  jj_kernel_body<4, EM>(A);
+  jj_kernel_body<4, EM, true>(A);
 }
 
 __global__ void jj_prepare_kernel(const sde_jj_point *pts, int n_points, int P,
