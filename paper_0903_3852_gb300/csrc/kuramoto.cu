@@ -346,20 +346,34 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
-// Wait (at most ~1 s) for the phase `parity` of an mbarrier; false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait (at most limit_ns) for the phase `parity` of an mbarrier; false on
+// expiry.  try_wait may suspend the thread for a while before it answers
+// (longer than a short limit: the hardware takes the suspend-time hint as a
+// hint only), so limits under a millisecond poll with the non-blocking
+// test_wait instead.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   const uint64_t t0 = now_ns();
+  const bool poll = limit_ns < 1000000ull;
   for (;;) {
     uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
+    if (poll)
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
+    else
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
     if (done) return true;
-    if (now_ns() - t0 > 1000000000ull) return false;
+    if (now_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -374,7 +388,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 // its sender had read the stage s slots, so a buffer is never overwritten
 // while it is read, and the receiver has re-armed the buffer's mbarrier
 // (after its own stage s wait, before its stage s + 1 sends) before any
-// stage s + 2 store can arrive.  Waits are bounded (~1 s): on expiry the kernel records
+// stage s + 2 store can arrive.  Waits are bounded (A.wait_ns, one second by
+// default): on expiry the kernel records
 // kErrTimeout, leaves the step loop (warp-uniformly) and meets the others at
 // the final cluster barrier.
 template <int OPT>
@@ -440,7 +455,7 @@ __global__ void __launch_bounds__(512, 1) kur_meanfield_async_kernel(const KurAr
                        b ? rslot1 : rslot0),
                    "r"(part.x), "r"(part.y), "r"(b ? rbar1 : rbar0)
                    : "memory");
-    const bool ok = mbar_wait_bounded(bar, parity);
+    const bool ok = mbar_wait_bounded(bar, parity, A.wait_ns);
     if (__any_sync(0xffffffffu, !ok)) {
       failed = true;
       if (lane == 0) atomicOr(A.err, kErrTimeout);
@@ -722,18 +737,32 @@ constexpr int kPairThreads = 128;
 constexpr int kPairPerThread = 2;  // receivers per thread: one packed FP32 pair
 constexpr int kPairTile = kPairThreads * kPairPerThread;
 
-// acc += sin(2 pi (t - ti)) for the thread's two receivers ti = (ti0, ti1),
-// phases in turns, on packed FP32 pairs: the difference d is reduced to
-// [-1/2, 1/2] by subtracting rint(d) (adding and subtracting 1.5 * 2^23 on
-// the FMA pipe, |d| < 2^22), so that the one special-function sin per
-// receiver sees an argument in [-pi, pi].  tt = (t, t), nti = (-ti0, -ti1).
-__device__ __forceinline__ void pair_terms2(float2 tt, float2 nti, float2 &acc) {
-  const float2 d = __fadd2_rn(tt, nti);
-  const float2 m = __fadd2_rn(__fadd2_rn(d, make_float2(12582912.0f, 12582912.0f)),
-                              make_float2(-12582912.0f, -12582912.0f));
-  const float2 r = __ffma2_rn(m, make_float2(-1.0f, -1.0f), d);
-  const float2 a = __fmul2_rn(r, make_float2(6.28318530717958647692f, 6.28318530717958647692f));
-  acc = __fadd2_rn(acc, make_float2(__sinf(a.x), __sinf(a.y)));
+// acc += sin(phi_j - phi_i) for the thread's two receivers i0, i1 and one
+// source j, all three phases as 32-bit fixed-point turns.  The difference is
+// taken exactly in integers and wraps to [-1/2, 1/2) turn by itself, so no
+// range reduction of a float is needed and no receiver carries the rounding
+// of its own phase into every one of its terms.  With x = d 2^-32 turns and
+// t = 1/4 - ||x| - 1/4| in [0, 1/4] (sin(pi - y) = sin y folds the outer
+// quarters onto the inner ones), sin(2 pi x) = sign(x) sin(2 pi t), and
+// sin(2 pi t) = t (S0 + S1 t^2 + ... + S4 t^8) with S0 the FP32 value of 2 pi;
+// S1..S4 minimise the largest absolute error on a dense grid of [0, 1/4] (a
+// linear program, fitted for this library).  In FP32 the result is within
+// 2.2e-7 of sin(2 pi x) (RMS 6e-8, no bias).  The polynomial runs on packed
+// FP32 pairs, both receivers per instruction, and the special-function unit
+// is not used: its sine's error is systematic enough to move phases by ~1e-5
+// over 10^3 steps of a partly synchronised population.
+__device__ __forceinline__ void pair_terms2(uint32_t tj, uint32_t ti0, uint32_t ti1, float2 &acc) {
+  const float2 x = __fmul2_rn(make_float2((float)(int32_t)(tj - ti0), (float)(int32_t)(tj - ti1)),
+                              make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f));  // 2^-32
+  const float2 u = __fadd2_rn(make_float2(fabsf(x.x), fabsf(x.y)), make_float2(-0.25f, -0.25f));
+  const float2 t = __fadd2_rn(make_float2(0.25f, 0.25f), make_float2(-fabsf(u.x), -fabsf(u.y)));
+  const float2 t2 = __fmul2_rn(t, t);
+  float2 p = __ffma2_rn(t2, make_float2(3.903203201e+01f, 3.903203201e+01f),
+                        make_float2(-7.653708649e+01f, -7.653708649e+01f));
+  p = __ffma2_rn(p, t2, make_float2(8.160352325e+01f, 8.160352325e+01f));
+  p = __ffma2_rn(p, t2, make_float2(-4.134174728e+01f, -4.134174728e+01f));
+  p = __ffma2_rn(p, t2, make_float2(6.283185482e+00f, 6.283185482e+00f));
+  acc = __ffma2_rn(make_float2(copysignf(t.x, x.x), copysignf(t.y, x.y)), p, acc);
 }
 
 // One SRK2 stage: receivers i of one replica in this CTA, all sources j
@@ -744,38 +773,42 @@ __device__ __forceinline__ void pair_terms2(float2 tt, float2 nti, float2 &acc) 
 // AdvanceSystem kernel of the Euler-Maruyama scheme.
 template <int STAGE>
 __global__ void __launch_bounds__(kPairThreads) kur_pairwise_stage(const KurPairArgs A) {
-  __shared__ float2 src_s[kPairTile];  // each source phase twice: (t, t)
+  __shared__ uint4 src_s[kPairTile / 4];  // source phases (fixed-point turns), four per entry
   const int rep = blockIdx.y;
   const int64_t N = A.N;
   const int64_t base = (int64_t)rep * N;
   const uint32_t *src = STAGE == 1 ? A.theta_t : A.theta;  // corrector: sums over theta~
-  float ti[kPairPerThread], acc[kPairPerThread];
+  uint32_t ti[kPairPerThread];
+  float acc[kPairPerThread];
   int64_t idx[kPairPerThread];
 #pragma unroll
   for (int k = 0; k < kPairPerThread; ++k) {
     idx[k] = (int64_t)blockIdx.x * kPairTile + threadIdx.x + k * kPairThreads;
-    ti[k] = idx[k] < N ? (float)(int32_t)src[base + idx[k]] * 2.3283064365386963e-10f : 0.0f;
+    ti[k] = idx[k] < N ? src[base + idx[k]] : 0u;
     acc[k] = 0.0f;
   }
   static_assert(kPairPerThread == 2, "the receivers of a thread form one packed pair");
-  const float2 nti = make_float2(-ti[0], -ti[1]);
+  uint32_t *src_w = reinterpret_cast<uint32_t *>(src_s);
   float2 acc2 = make_float2(0.0f, 0.0f);
   for (int64_t j0 = 0; j0 < N; j0 += kPairTile) {
     const int cnt = (N - j0) < kPairTile ? (int)(N - j0) : kPairTile;
 #pragma unroll
     for (int k = 0; k < kPairPerThread; ++k) {
       const int jj = threadIdx.x + k * kPairThreads;
-      if (jj < cnt) {
-        const float t = (float)(int32_t)src[base + j0 + jj] * 2.3283064365386963e-10f;
-        src_s[jj] = make_float2(t, t);
-      }
+      if (jj < cnt) src_w[jj] = src[base + j0 + jj];
     }
     __syncthreads();
     if (cnt == kPairTile) {
-#pragma unroll 8
-      for (int jj = 0; jj < kPairTile; ++jj) pair_terms2(src_s[jj], nti, acc2);
+#pragma unroll 2
+      for (int q = 0; q < kPairTile / 4; ++q) {
+        const uint4 t4 = src_s[q];
+        pair_terms2(t4.x, ti[0], ti[1], acc2);
+        pair_terms2(t4.y, ti[0], ti[1], acc2);
+        pair_terms2(t4.z, ti[0], ti[1], acc2);
+        pair_terms2(t4.w, ti[0], ti[1], acc2);
+      }
     } else {
-      for (int jj = 0; jj < cnt; ++jj) pair_terms2(src_s[jj], nti, acc2);
+      for (int jj = 0; jj < cnt; ++jj) pair_terms2(src_w[jj], ti[0], ti[1], acc2);
     }
     __syncthreads();
   }
@@ -1110,7 +1143,7 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   sde_status st = SDE_OK;
   cudaError_t e;
-  if ((e = cudaMalloc((void **)&omega, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = device_alloc((void **)&omega, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) st = cuda_fail(e, "stream");
   if (st == SDE_OK && (e = cudaEventCreate(&e0)) != cudaSuccess) st = cuda_fail(e, "event");
   if (st == SDE_OK && (e = cudaEventCreate(&e1)) != cudaSuccess) st = cuda_fail(e, "event");
@@ -1133,6 +1166,7 @@ sde_status meanfield_autotune(KuramotoCtx *k, int only_cs, bool with_grid) {
     a.sc = 1e-3f;
     a.seed = 0;
     a.err = k->err;
+    a.wait_ns = k->wait_ns;
     float best = 1e30f;
     for (const MfShape &c : cands) {
       float tmin = 1e30f;
@@ -1232,7 +1266,7 @@ sde_status kuramoto_create(const sde_config *cfg, int sm_count, uint32_t *err, K
   cudaError_t e;
   auto alloc = [&](void **p, size_t bytes) {
     if (st != SDE_OK) return;
-    if ((e = cudaMalloc(p, bytes ? bytes : 1)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
+    if ((e = device_alloc(p, bytes ? bytes : 1)) != cudaSuccess) st = cuda_fail(e, "cudaMalloc");
   };
   alloc((void **)&k->theta, NR * 4);
   // the grid-wide form is a candidate when few replicas leave SMs idle
@@ -1348,6 +1382,10 @@ bool kuramoto_kernel_stats(KuramotoCtx *k, float *mean_ms, float *total_ms, int6
   return true;
 }
 
+void kuramoto_set_wait_limit(KuramotoCtx *k, uint64_t ns) {
+  if (k) k->wait_ns = ns;
+}
+
 void kuramoto_destroy(KuramotoCtx *k) {
   if (!k) return;
   cudaDeviceSynchronize();
@@ -1375,7 +1413,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
     cudaFree(obs_in);
     *obs = nullptr;
     *max_rows = 0;
-    SDE_CUDA_TRY(cudaMalloc((void **)obs, sizeof(sde_obs_row) * n_rows));
+    SDE_CUDA_TRY(device_alloc((void **)obs, sizeof(sde_obs_row) * n_rows));
     *max_rows = n_rows;
   }
   double *rbuf = r->r_out_dev;
@@ -1384,7 +1422,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
       cudaFree(k->r_scratch);
       k->r_scratch = nullptr;
       k->r_scratch_rows = 0;
-      SDE_CUDA_TRY(cudaMalloc((void **)&k->r_scratch, sizeof(double) * n_rows * k->R));
+      SDE_CUDA_TRY(device_alloc((void **)&k->r_scratch, sizeof(double) * n_rows * k->R));
       k->r_scratch_rows = n_rows;
     }
     rbuf = k->r_scratch;
@@ -1416,6 +1454,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
     a.sc = (float)(sqrt(2.0 * k->D * k->dt) * inv2pi);
     a.seed = k->seed;
     a.err = k->err;
+    a.wait_ns = k->wait_ns;
     SDE_CUDA_TRY(launch_meanfield(a, k->block, k->opt, k->cs, k->mf_async, s));
   } else if (k->model == SDE_KURAMOTO_PAIRWISE) {
     KurPairArgs a{};
