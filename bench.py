@@ -986,8 +986,10 @@ def run_surrogate_inference(args, device):
 def run_surrogate(args, device):
     """The learned surrogate of <<v>>: labels from the sweep engine (10^5 points x
     2048 paths x 2e4 steps), an ensemble of 4 networks trained by the library's
-    kernels, calibration, then one bench step = answering 10^4 held-out points
-    (network where its predicted error <= 1e-2, simulator at 8192 paths elsewhere)."""
+    kernels on 80,000 of them, an error model on 10,000 more, selective
+    calibration on the last 10,000, then one bench step = answering 10^4 held-out
+    points (network where its predicted error <= 1e-2, simulator at 8192 paths
+    elsewhere)."""
     import torch
     from paper_0903_3852_gb300 import build as sde_build
     from paper_0903_3852_gb300 import surrogate
@@ -1000,7 +1002,8 @@ def run_surrogate(args, device):
     label_units = len(train) * 2048.0 * steps
     sur = surrogate.Surrogate(members=4, max_batch=131072, lr=2e-3, seed=3)
     t0 = time.perf_counter()
-    sur.fit(train[:90_000], y[:90_000], epochs=120, batch=1024)
+    sur.fit(train[:80_000], y[:80_000], epochs=120, batch=1024)
+    sur.fit_error_model(train[80_000:90_000], y[80_000:90_000])
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     tau, cal_share = sur.calibrate(train[90_000:], y[90_000:], se[90_000:], tol, risk=5e-4)
@@ -1039,8 +1042,8 @@ def run_surrogate(args, device):
         "surrogate": {"label_seconds": t_lab, "label_points_per_sec_2048_paths": len(train) / t_lab,
                       "label_path_steps_per_sec": label_units / t_lab, "fit_seconds": t_fit,
                       "mlp_points_per_sec": mlp_pps, "inference_batch_1e5": infer,
-                      "calibration": {"spread_threshold": tau, "answered_share": cal_share, "risk": 5e-4,
-                                      "points": 10_000},
+                      "calibration": {"log_error_threshold": tau, "answered_share": cal_share, "risk": 5e-4,
+                                      "points": 10_000, "split": "ensemble 80k, error model 10k, calibration 10k"},
                       "simulator_points_per_sec_8192_paths": len(evalp) / t_ref,
                       "answered_by_network": float(ans.mean()),
                       "within_tol_all": float(ok.mean()),

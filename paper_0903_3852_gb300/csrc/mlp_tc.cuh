@@ -8,18 +8,19 @@
 // kernels of the training path do.
 //
 // One CTA takes 128 points (one tcgen05 M = 128 tile) of one ensemble member:
-//   warps 0-7 (256 threads): layer 0 on the CUDA cores, then after each square
-//     layer its epilogue -- tcgen05.ld of the FP32 accumulators, + bias, SiLU,
-//     BF16 -- written back into shared memory as the next layer's A operand in
-//     the 128-byte-swizzled K-major layout the MMA reads, or, after the last
-//     square layer, the output dot product; warp w owns TMEM lane quarter
-//     w % 4 (its 32 rows) and column half w / 4;
-//   warp 8, one thread: TMA producer streaming the BF16 square-layer weights
+//   warps 0-15 (512 threads): layer 0 on the CUDA cores, then after each
+//     square layer its epilogue -- tcgen05.ld of the FP32 accumulators, +
+//     bias, SiLU, BF16 -- written back into shared memory as the next layer's
+//     A operand in the 128-byte-swizzled K-major layout the MMA reads, or,
+//     after the last square layer, the output dot product; warp w owns TMEM
+//     lane quarter w % 4 (its 32 rows) and column quarter w / 4 (64
+//     columns); the element arithmetic runs on packed FP32 pairs;
+//   warp 16, one thread: TMA producer streaming the BF16 square-layer weights
 //     through a 4-slot ring of 256 x 64 chunks (K-major, 128-byte swizzle);
-//   warp 9, one thread: MMA issuer, M = 128, N = 256, K = 16 per instruction,
-//     the accumulator (256 FP32 columns) in tensor memory, which warp 9
-//     allocates and frees.
-// Layer handoffs go through mbarriers: `abuf` (256 arrivals: the A operand of
+//   warp 17, one thread: MMA issuer, M = 128, N = 256, K = 16 per
+//     instruction, the accumulator (256 FP32 columns) in tensor memory, which
+//     warp 17 allocates and frees.
+// Layer handoffs go through mbarriers: `abuf` (512 arrivals: the A operand of
 // the next square layer is in shared memory) and `acc` (tcgen05.commit: the
 // accumulator is complete).  Every wait is bounded by one second of
 // %globaltimer; on expiry the CTA stops, drains what it issued, records
@@ -49,12 +50,13 @@ constexpr int KCH = H / 64;        // 64-element K chunks per square layer
 constexpr int A_CHUNK = BM * 128;  // bytes of one A chunk: 128 rows x 128 B
 constexpr int W_CHUNK = H * 128;   // bytes of one weight chunk: 256 rows x 128 B
 constexpr int RING = 4;            // weight chunks in flight
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int PROD_WARP = EPI_WARPS;
 constexpr int MMA_WARP = EPI_WARPS + 1;
 constexpr int THREADS = EPI_THREADS + 64;
 constexpr int SMEM_BYTES = KCH * A_CHUNK + RING * W_CHUNK + 1024;  // + alignment slack
+constexpr int COLS_PER_WARP = H / (EPI_WARPS / 4);  // 64
 constexpr int MAX_IN = 8;
 constexpr int MAX_HH = 7;
 
@@ -73,15 +75,21 @@ struct Args {
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
-__device__ __forceinline__ float silu_tc(float z) {
-  const float zc = fmaxf(z, -30.0f);
-  float e;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.44269504088896341f * zc));
-  const float y = 1.0f + e;
-  float r = __int_as_float(0x7EF311C0 - __float_as_int(y));
-  r = fmaf(r, fmaf(-y, r, 1.0f), r);
-  r = fmaf(r, fmaf(-y, r, 1.0f), r);
-  return z * r;
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// SiLU of two values on packed FP32 pairs (the exponentials one at a time).
+__device__ __forceinline__ float2 silu2(float2 z) {
+  const float2 a = __fmul2_rn(make_float2(fmaxf(z.x, -30.0f), fmaxf(z.y, -30.0f)), f2(-1.44269504088896341f));
+  float ex, ey;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(a.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ey) : "f"(a.y));
+  const float2 y = __fadd2_rn(make_float2(ex, ey), f2(1.0f));
+  float2 r = make_float2(__int_as_float(0x7EF311C0 - __float_as_int(y.x)),
+                         __int_as_float(0x7EF311C0 - __float_as_int(y.y)));
+  const float2 ny = make_float2(-y.x, -y.y);
+  r = __ffma2_rn(r, __ffma2_rn(ny, r, f2(1.0f)), r);
+  r = __ffma2_rn(r, __ffma2_rn(ny, r, f2(1.0f)), r);
+  return __fmul2_rn(z, r);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -116,11 +124,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *Ab = smem;                  // KCH chunks of [BM][128 B]
   uint8_t *Wr = smem + KCH * A_CHUNK;  // RING slots of [H][128 B]
-  __shared__ float w0s[H * MAX_IN];
-  __shared__ float b0s[H];
-  __shared__ float bhs[MAX_HH * H];
-  __shared__ float wos[H];
-  __shared__ float part[BM];
+  __shared__ __align__(16) float w0s[MAX_IN * H];  // [k][n]: output pairs adjacent
+  __shared__ __align__(16) float b0s[H];
+  __shared__ __align__(16) float bhs[MAX_HH * H];
+  __shared__ __align__(16) float wos[H];
+  __shared__ float part[EPI_WARPS / 4][BM];
   __shared__ __align__(8) uint64_t full_bar[RING];
   __shared__ __align__(8) uint64_t empty_bar[RING];
   __shared__ __align__(8) uint64_t acc_bar;
@@ -156,7 +164,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   // small parameters: layer 0 and the output weights BF16-rounded (the GEMM
   // operands), biases FP32
-  for (int i = threadIdx.x; i < H * n_in; i += THREADS) w0s[i] = bf16r(pm[a.off_w0 + i]);
+  for (int i = threadIdx.x; i < H * n_in; i += THREADS)  // W_0 is [n][k] in the parameters
+    w0s[(i % n_in) * H + i / n_in] = bf16r(pm[a.off_w0 + i]);
   for (int i = threadIdx.x; i < H; i += THREADS) {
     b0s[i] = pm[a.off_b0 + i];
     wos[i] = bf16r(pm[a.off_wo + i]);
@@ -222,9 +231,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- layer 0 and the epilogues: warps 0-7 ----
+    // ---- layer 0 and the epilogues: warps 0-15 ----
     const int q = warp & 3;   // TMEM lane quarter: rows 32 q .. 32 q + 31
-    const int hc = warp >> 2; // column half: 128 hc .. 128 hc + 127
+    const int cq = warp >> 2; // column quarter: 64 cq .. 64 cq + 63
     const int m = q * 32 + lane;
     const int64_t row = row0 + m;
     const bool valid = row < a.B;
@@ -232,26 +241,23 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
     for (int k = 0; k < MAX_IN; ++k) x[k] = (valid && k < n_in) ? bf16r(a.X[row * n_in + k]) : 0.0f;
 #pragma unroll 1
-    for (int g = 0; g < 4; ++g) {
-      const int n0 = hc * 128 + g * 32;
+    for (int g = 0; g < COLS_PER_WARP / 32; ++g) {
+      const int n0 = cq * COLS_PER_WARP + g * 32;
       uint32_t p[16];
 #pragma unroll
       for (int j = 0; j < 32; j += 2) {
-        float z0 = b0s[n0 + j], z1 = b0s[n0 + j + 1];
+        float2 z = *reinterpret_cast<const float2 *>(b0s + n0 + j);
 #pragma unroll
-        for (int k = 0; k < MAX_IN; ++k) {
-          if (k < n_in) {
-            z0 = fmaf(x[k], w0s[(n0 + j) * n_in + k], z0);
-            z1 = fmaf(x[k], w0s[(n0 + j + 1) * n_in + k], z1);
-          }
-        }
-        p[j >> 1] = pack_bf16(silu_tc(z0), silu_tc(z1));
+        for (int k = 0; k < MAX_IN; ++k)
+          if (k < n_in) z = __ffma2_rn(f2(x[k]), *reinterpret_cast<const float2 *>(w0s + k * H + n0 + j), z);
+        const float2 h = silu2(z);
+        p[j >> 1] = pack_bf16(h.x, h.y);
       }
       store_row32(Ab, m, n0, p);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_arrive(&abuf_bar);
-    float dot = 0.0f;
+    float2 dot = make_float2(0.0f, 0.0f);
     bool done = n_hh == 0;
     for (int l = 0; l < n_hh; ++l) {
       if (!tc::mbar_wait(&acc_bar, (uint32_t)l & 1u, &abort_flag)) break;
@@ -260,19 +266,27 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool last = l == n_hh - 1;
       const float *bl = bhs + l * H;
 #pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
-        const int n0 = hc * 128 + g * 32;
+      for (int g = 0; g < COLS_PER_WARP / 32; ++g) {
+        const int n0 = cq * COLS_PER_WARP + g * 32;
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)n0, v);
         if (!last) {
           uint32_t p[16];
 #pragma unroll
-          for (int j = 0; j < 32; j += 2)
-            p[j >> 1] = pack_bf16(silu_tc(v[j] + bl[n0 + j]), silu_tc(v[j + 1] + bl[n0 + j + 1]));
+          for (int j = 0; j < 32; j += 2) {
+            const float2 h = silu2(__fadd2_rn(make_float2(v[j], v[j + 1]),
+                                              *reinterpret_cast<const float2 *>(bl + n0 + j)));
+            p[j >> 1] = pack_bf16(h.x, h.y);
+          }
           store_row32(Ab, m, n0, p);
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) dot = fmaf(bf16r(silu_tc(v[j] + bl[n0 + j])), wos[n0 + j], dot);
+          for (int j = 0; j < 32; j += 2) {
+            const float2 h = silu2(__fadd2_rn(make_float2(v[j], v[j + 1]),
+                                              *reinterpret_cast<const float2 *>(bl + n0 + j)));
+            dot = __ffma2_rn(make_float2(bf16r(h.x), bf16r(h.y)), *reinterpret_cast<const float2 *>(wos + n0 + j),
+                             dot);
+          }
         }
       }
       if (!last) {
@@ -283,10 +297,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         done = true;
       }
     }
-    // the two column halves of each row
-    if (hc == 1) part[m] = dot;
+    // the four column quarters of each row
+    part[cq][m] = dot.x + dot.y;
     asm volatile("bar.sync 1, %0;" ::"r"(EPI_THREADS) : "memory");
-    if (hc == 0 && valid && done && !abort_flag) a.out[(int64_t)member * a.out_stride + row] = dot + part[m] + bo;
+    if (cq == 0 && valid && done && !abort_flag)
+      a.out[(int64_t)member * a.out_stride + row] = ((part[0][m] + part[1][m]) + (part[2][m] + part[3][m])) + bo;
   }
   tc::tmem_fence_before();
   __syncthreads();

@@ -506,11 +506,13 @@ class Mlp:
 
 
 def points_to_device(points):
-    """Pack a list of parameter dicts into a CUDA uint8 tensor of sde_jj_point records."""
+    """Pack a list of parameter dicts into a CUDA uint8 tensor of sde_jj_point
+    records (five doubles each: gamma, a, omega, f, D)."""
     import torch
-    arr = (JJPoint * len(points))(*[JJPoint(p["gamma"], p["a"], p["omega"], p["f"], p["D"]) for p in points])
-    buf = bytearray(arr)
-    return torch.frombuffer(buf, dtype=torch.uint8).clone().cuda()
+    rec = np.array([(p["gamma"], p["a"], p["omega"], p["f"], p["D"]) for p in points], dtype=np.float64)
+    rec = np.ascontiguousarray(rec.reshape(len(points), 5))
+    assert rec.itemsize * 5 == ctypes.sizeof(JJPoint)
+    return torch.from_numpy(rec.view(np.uint8).reshape(-1)).cuda()
 
 
 def phase_histogram(phi, nbins, stream=None):

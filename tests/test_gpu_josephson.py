@@ -90,8 +90,13 @@ def test_pathwise_fig2_regime_sensitivity_gated():
     calm = d <= 1e-6
     print("fig2 @1000: %d/%d within 1e-5, %d calm (max err %.2e), median err %.2e vs median d %.2e"
           % ((err <= 1e-5).sum(), n, calm.sum(), err[calm].max(initial=0), np.median(err), np.median(d)))
+    print("fig2 @1000: max over paths of (err - 1e-5) / d = %.2f" % np.max((err - 1e-5) / np.maximum(d, 1e-30)))
     assert err[calm].max(initial=0) <= 1e-5
-    assert np.all(err <= 1e-5 + 100.0 * d)
+    # d injects 6e-8 relative per step; the kernel's largest per-step departure
+    # from exact arithmetic is its Box-Muller radius error (<= 2.2e-4 absolute,
+    # scaled by s = sqrt(2 gamma D dt) = 3.4e-3 here: 7.5e-7 in v), 12.5 times
+    # that jitter, so an FP32 path may sit up to ~12.5 d from the oracle
+    assert np.all(err <= 1e-5 + 12.5 * d)
     assert np.median(err) <= np.median(d)
 
 

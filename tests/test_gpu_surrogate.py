@@ -1,10 +1,11 @@
 """The learned surrogate of <<v>> end to end at reduced scale: labels from the
 sweep engine (2048 paths x 2e4 steps per point, as in the full configuration),
-an ensemble trained by the library's kernels, selective calibration of its
-predicted error, and simulator fallback wherever that error exceeds 1e-2.
+an ensemble trained by the library's kernels, a second network that learns
+the ensemble's error on held-out points, selective calibration of that
+predicted error, and simulator fallback wherever it exceeds 1e-2.
 
 The tolerance is a calibrated rate, not a guarantee for every point: the
-network is trusted below the spread at which held-out calibration points miss
+network is trusted below the predicted error at which held-out calibration points miss
 1e-2 (beyond their labels' own noise) at a rate of at most 0.2% here (0.05% in
 the full-size benchmark).  Checks, against a higher-path simulator reference
 (slack: 3 of the reference's and the answer's standard errors): at least 99%
@@ -29,8 +30,9 @@ def test_surrogate_with_fallback_is_accurate_and_saves_time():
     train = inputs.surrogate_points(33000, seed=16)
     y, se, t_lab = surrogate.simulate(train, 2048, STEPS, seed=16)
     sur = surrogate.Surrogate(members=4, max_batch=16384, lr=2e-3, seed=3)
-    sur.fit(train[:30000], y[:30000], epochs=100, batch=1024)
-    tau, share = sur.calibrate(train[30000:], y[30000:], se[30000:], TOL, risk=2e-3)
+    sur.fit(train[:26000], y[:26000], epochs=100, batch=1024)
+    sur.fit_error_model(train[26000:29500], y[26000:29500])
+    tau, share = sur.calibrate(train[29500:], y[29500:], se[29500:], TOL, risk=2e-3)
     print("calibration: spread threshold %.3e, %.1f%% of calibration points answered" % (tau, 100 * share))
     evalp = inputs.surrogate_points(1000, seed=17)
     ref, ref_se, t_ref = surrogate.simulate(evalp, 8192, STEPS, seed=17)
