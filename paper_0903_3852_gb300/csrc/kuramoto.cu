@@ -74,7 +74,14 @@ __device__ __forceinline__ float2 block_sum2(float a, float b, float2 *red) {
 constexpr float kQuant = 131072.0f;
 constexpr float kInvQuant = 1.0f / 131072.0f;
 
-__device__ __forceinline__ int quant(float v) { return __float2int_rn(v * kQuant); }
+// round(v 2^17) to the nearest integer (ties to even) for |v| <= 1, on the FMA
+// pipe: v 2^17 + 1.5 2^23 lies in [2^23, 2^24), where the FP32 spacing is 1,
+// so the one rounding of the FMA is the rounding to an integer, read off the
+// mantissa bits.  The same integer as __float2int_rn(v * 2^17), without the
+// conversion unit.
+__device__ __forceinline__ int quant(float v) {
+  return __float_as_int(fmaf(v, kQuant, 12582912.0f)) - 0x4B400000;
+}
 
 __device__ __forceinline__ int2 warp_qsum(int a, int b) {
   return make_int2(__reduce_add_sync(0xffffffffu, a), __reduce_add_sync(0xffffffffu, b));
