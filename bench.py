@@ -84,8 +84,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="sweep: skip the plain per-path kernel comparison of the default line")
-    ap.add_argument("--fused", action="store_true",
-                    help="general coupling, tensor-core form: SRK2 sub-steps in the GEMM epilogue")
+    ap.add_argument("--separate-stage", action="store_true",
+                    help="general coupling, tensor-core form: SRK2 sub-steps as separate kernels instead of "
+                         "in the GEMM epilogue (the default)")
+    ap.add_argument("--gemm-single-cta", action="store_true",
+                    help="general coupling, tensor-core form: one CTA per 128 x 256 GEMM tile instead of "
+                         "the CTA-pair GEMM (256 x 256 per cluster of two CTAs)")
     return ap.parse_args()
 
 
@@ -429,7 +433,9 @@ def run_ours(args, rank, world, device):
         model = sde.SDE_KURAMOTO_GENERAL if tc else sde.SDE_KURAMOTO_GENERAL_FP32
         S = args.general_steps or (w["steps"] if tc else 100)
         N, R = w["n_osc"], w["replicas"]
-        flags = sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_FUSED if args.fused else 0)
+        fused = tc and not args.separate_stage
+        flags = (sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_FUSED if fused else 0)
+                 | (sde.SDE_FLAG_GEMM_SINGLE_CTA if args.gemm_single_cta else 0))
         ens = sde.Ensemble.kuramoto(model, N, R, 0.0, w["D"], w["dt"], w["seed"],
                                     sample_every=w["sample_every"], flags=flags)
         Kdev = torch.from_numpy(w["Kmat"]).to(device)
@@ -455,9 +461,12 @@ def run_ours(args, rank, world, device):
         flop_per_launch = 2.0 * N * (2 * R) * N  # one GEMM K . [sin | cos]
         launches_per_step = 4 * S + S // w["sample_every"] + 4
         cfg = {"workload": kuramoto_workload_name(args.workload, False, N, R),
-               "stage": "fused into the GEMM epilogue" if args.fused else "separate kernel",
+               "stage": "fused into the GEMM epilogue" if fused else "separate kernel",
                "steps_per_bench_step": S, "K0": w["K0"], "D": w["D"], "dt": w["dt"],
                "gemm": "M=%d N=%d K=%d per stage, 2 per step" % (N, 2 * R, N),
+               "gemm_tiling": ({2: "256 x 256 per CTA pair (tcgen05 cta_group::2)",
+                                1: "128 x %d per CTA (tcgen05 cta_group::1)" % ens.tuning()[1]}[ens.tuning()[2]]
+                               if tc else "128 x 128 per CTA (FP32 FMA)"),
                "l2": "K matrix %d MiB streams each GEMM; flushed between steps (256 MiB write)"
                      % (N * N * (2 if tc else 4) >> 20)}
 
@@ -561,9 +570,6 @@ def run_ours(args, rank, world, device):
     elif args.workload == "kuramoto-fig4":
         traffic = 16.6 * w["n_osc"] * w["replicas"]  # mean over the launches of 4 steps
         traffic_src = "ncu capture of the grid-wide mean-field launches"
-    elif args.workload == "kuramoto-general" and not args.fused:
-        traffic = 146.2e6  # K (134 MB) once + operands and output
-        traffic_src = "ncu capture of the tensor-core GEMM"
     elif args.workload == "kuramoto-meanfield":
         traffic = 2.43e6  # phases and omega read once per run; results stay in L2
         traffic_src = "ncu capture of the cluster mean-field kernel"

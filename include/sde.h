@@ -80,6 +80,11 @@ typedef enum sde_schedule {
                                         by asynchronous remote stores that complete on the
                                         receiving CTA's mbarrier, instead of a cluster barrier
                                         (the autotuner tries both forms when unset) */
+#define SDE_FLAG_GEMM_SINGLE_CTA 32u /* general coupling, tensor-core form: one CTA per 128 x 256
+                                        tile of the GEMM (tcgen05 cta_group::1) instead of the
+                                        CTA-pair GEMM (a 256 x 256 tile per cluster of two CTAs,
+                                        cta_group::2) that runs by default where n_osc % 256 == 0
+                                        and n_replicas % 128 == 0 (same results bit for bit) */
 #define SDE_FLAG_EULER 8u        /* Euler-Maruyama instead of SRK2 (Alg. 2): the
                                     first-order scheme of PROG2 (Sec. 4.2).
                                     Josephson: every schedule, same kernels with
@@ -252,7 +257,9 @@ const char *sde_last_error(void);
    (Josephson; values 11 and 12 mean 1 and 2 with registers capped at 64) or
    oscillators (Kuramoto) per thread, and CTAs per replica (the thread-block
    cluster of the mean-field kernel; 0 for the grid-wide mean field, whose
-   per-thread count is then the oscillators each thread strides over; 1
+   per-thread count is then the oscillators each thread strides over; for the
+   general coupling's tensor-core GEMM, the CTAs per tile: 2 for the CTA-pair
+   GEMM, whose per-thread value is then the D columns of a tile; 1
    otherwise).  Any pointer may be NULL. */
 sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads, int32_t *per_thread,
                           int32_t *cluster_ctas);

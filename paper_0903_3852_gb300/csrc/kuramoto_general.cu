@@ -58,7 +58,7 @@ __global__ void kg_operand_kernel(const uint32_t *theta, T *op, int64_t N) {
 
 // One SRK2 stage for every (replica, oscillator) from the GEMM output Dt
 // (the forms without the fused epilogue): the same per-element update as the
-// tensor-core epilogue (tc::stage_element), the next operand written as T.
+// tensor-core epilogue (tc::stage_group), the next operand written as T.
 // Grid: (N / 256, R).
 // kStageIlp elements per thread (i, i + 256, ...): every input of the group is
 // loaded before any arithmetic, so each thread keeps several loads in flight.
@@ -207,8 +207,10 @@ sde_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t co
 
 struct GemmPlan {
   CUtensorMap mapK;
-  CUtensorMap mapOp[2];
+  CUtensorMap mapOp[2];  // box of bn rows (one CTA's tile)
+  CUtensorMap mapOpHalf[2];  // box of 128 rows (one CTA's half of a pair tile)
   int bn = 0;
+  bool pair = false;  // CTA-pair GEMM (tc_gemm2_bf16_kernel)
 };
 
 bool is_tc(const KuramotoCtx *k) { return k->model == SDE_KURAMOTO_GENERAL; }
@@ -248,6 +250,15 @@ void launch_tc(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t 
       g->mapK, g->mapOp[which], k->P, M, Kdim, k->err, sa, k->wait_ns);
 }
 
+template <int EPI>
+void launch_tc2(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
+  GemmPlan *g = (GemmPlan *)k->gemm_plan;
+  const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
+  dim3 grid(M / tc::BM, Ncols / tc::BN2);  // clusters of two CTAs along x
+  tc::tc_gemm2_bf16_kernel<EPI><<<grid, tc::EpiThreads<EPI>::value, tc::SMEM2_BYTES, s>>>(
+      g->mapK, g->mapOpHalf[which], k->P, M, Kdim, k->err, sa, k->wait_ns);
+}
+
 // GEMM reading operand buffer `which`; epi = EPI_STORE_D writes Dt, the stage
 // epilogues apply the SRK2 sub-step and write operand buffer 1 - which.
 cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s, int epi = tc::EPI_STORE_D,
@@ -256,7 +267,11 @@ cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s, int epi = tc:
   if (is_tc(k)) {
     GemmPlan *g = (GemmPlan *)k->gemm_plan;
     const tc::StageArgs sa = stage_args(k, epi == tc::EPI_STORE_D ? -1 : 1 - which, omega, n, run_begin);
-    if (g->bn == 256) {
+    if (g->pair) {
+      if (epi == tc::EPI_STAGE0) launch_tc2<tc::EPI_STAGE0>(k, which, sa, s);
+      else if (epi == tc::EPI_STAGE1) launch_tc2<tc::EPI_STAGE1>(k, which, sa, s);
+      else launch_tc2<tc::EPI_STORE_D>(k, which, sa, s);
+    } else if (g->bn == 256) {
       if (epi == tc::EPI_STAGE0) launch_tc<256, tc::EPI_STAGE0>(k, which, sa, s);
       else if (epi == tc::EPI_STAGE1) launch_tc<256, tc::EPI_STAGE1>(k, which, sa, s);
       else launch_tc<256, tc::EPI_STORE_D>(k, which, sa, s);
@@ -324,10 +339,13 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
     GemmPlan *g = new GemmPlan();
     k->gemm_plan = g;
     g->bn = (2 * k->R) % 256 == 0 ? 256 : 128;
+    g->pair = k->N % 256 == 0 && (2 * k->R) % tc::BN2 == 0 && !(k->flags & SDE_FLAG_GEMM_SINGLE_CTA);
     sde_status st = make_map(&g->mapK, k->Kbf16, k->N, k->N, tc::BM);
     if (st != SDE_OK) return st;
     for (int w = 0; w < 2; ++w) {
       st = make_map(&g->mapOp[w], op_buf(k, w), 2 * k->R, k->N, g->bn);
+      if (st != SDE_OK) return st;
+      st = make_map(&g->mapOpHalf[w], op_buf(k, w), 2 * k->R, k->N, tc::BH2);
       if (st != SDE_OK) return st;
     }
     const void *kernels[] = {
@@ -342,12 +360,20 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
                                     q < 3 ? tc::Shape<256>::SMEM_BYTES : tc::Shape<128>::SMEM_BYTES)) !=
           cudaSuccess)
         return cuda_fail(e, "cudaFuncSetAttribute");
+    const void *kernels2[] = {(const void *)tc::tc_gemm2_bf16_kernel<tc::EPI_STORE_D>,
+                              (const void *)tc::tc_gemm2_bf16_kernel<tc::EPI_STAGE0>,
+                              (const void *)tc::tc_gemm2_bf16_kernel<tc::EPI_STAGE1>};
+    for (int q = 0; q < 3; ++q)
+      if ((e = cudaFuncSetAttribute(kernels2[q], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::SMEM2_BYTES)) != cudaSuccess)
+        return cuda_fail(e, "cudaFuncSetAttribute");
   } else {
     if ((e = device_alloc((void **)&k->Kf32, NN * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = device_alloc((void **)&k->Bt32, NR * 2 * 4 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   }
   k->block = is_tc(k) ? tc::THREADS : 256;
   k->opt = is_tc(k) ? ((GemmPlan *)k->gemm_plan)->bn : SG_BN;
+  k->cs = (is_tc(k) && ((GemmPlan *)k->gemm_plan)->pair) ? 2 : 1;  // CTAs per GEMM tile
   return SDE_OK;
 }
 

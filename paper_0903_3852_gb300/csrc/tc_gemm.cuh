@@ -116,12 +116,88 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
   }
 }
 
+// Address of the same shared-memory variable in the CTA of cluster rank
+// `rank` (shared::cluster window).
+__device__ __forceinline__ uint32_t mapa_shared(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+  return r;
+}
+
+// Count `bytes` as transferred on a local mbarrier's current phase without a
+// transfer (for a share of a slot that will never be loaded).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ int ld_shared_cluster_s32(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Every thread of every CTA of the cluster: arrive (release) and wait
+// (acquire).  The forms without .aligned: threads of a warp may reach it
+// from a bounded wait loop at different iterations.
+__device__ __forceinline__ void cluster_barrier() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
                                             int c1) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
       "[%2];" ::"r"(smem_addr(dst)),
       "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// An L2 policy that evicts first what it tags: for the coupling matrix, which
+// every GEMM streams once (read by the CTAs of one tile row at about the
+// same time), so that it does not push the SRK2 state the epilogues read out
+// of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void tma_load_2d_hint(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "l"(policy)
+      : "memory");
+}
+
+// The same load for a CTA of a pair: the data lands in this CTA's shared
+// memory, the byte count completes on the mbarrier at shared::cluster address
+// `bar` (the even CTA's).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar, int c0,
+                                                 int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, "
+      "{%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_pair_hint(void *dst, const CUtensorMap *map, uint32_t bar, int c0,
+                                                      int c1, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2.L2::"
+      "cache_hint [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "l"(policy)
       : "memory");
 }
 
@@ -156,6 +232,30 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_addr(bar))
                : "memory");
+}
+
+// The CTA-pair forms (cta_group::2): one MMA of M = 256 rows over the two
+// CTAs of a pair, issued by the even CTA; each CTA supplies its own 128 rows
+// of A and half of the N rows of B at the same shared-memory offsets as the
+// issuer's descriptors, and receives its 128 rows of D in its own tensor
+// memory at the same column address.
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Arrive once on the mbarrier at this offset in both CTAs of the pair when
+// every pair MMA issued before has completed.
+__device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_addr(bar)),
+      "h"((uint16_t)3)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_fence_before() {
@@ -272,22 +372,32 @@ __device__ __forceinline__ void stage_store(const StageArgs &a, T *op_next, int6
   store_operand(op_next, (2 * r + 1) * a.N + i, o.co);
 }
 
-template <int STAGE, typename T>
-__device__ __forceinline__ void stage_element(const StageArgs &a, T *op_next, int64_t r, int64_t i, float ps,
-                                              float pc, uint2 key) {
-  const int64_t idx = r * a.N + i;
-  const uint32_t th = a.theta[idx];
-  const uint32_t th_s = STAGE == 0 ? th : a.theta_t[idx];
-  const float psi = stage_noise<STAGE>(a, r, i, idx, key);
-  const float g1 = STAGE == 1 ? a.g1[idx] : 0.0f;
-  const StageOut o = stage_math<STAGE>(a, th_s, th, a.omega[idx], psi, g1, ps, pc);
-  stage_store<STAGE>(a, op_next, r, i, idx, o);
+// NB consecutive replicas r0 .. r0 + NB - 1 of oscillator i, their coupling
+// components in v[2j], v[2j + 1]: every input of the group is loaded before
+// any arithmetic or store (the stores may alias the inputs as far as the
+// compiler knows), so NB loads of each array are in flight at once.
+template <int STAGE, int NB>
+__device__ __forceinline__ void stage_group(const StageArgs &a, int64_t r0, int64_t i, const float *v, uint2 key) {
+  uint32_t th[NB], th_s[NB];
+  float om[NB], psi[NB], g1[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const int64_t idx = (r0 + j) * a.N + i;
+    th[j] = a.theta[idx];
+    th_s[j] = STAGE == 0 ? th[j] : a.theta_t[idx];
+    om[j] = a.omega[idx];
+    g1[j] = STAGE == 1 ? a.g1[idx] : 0.0f;
+    psi[j] = (STAGE == 0 && a.fresh) ? 0.0f : a.psi4[(a.n & 3) * a.NR + idx];
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const int64_t r = r0 + j, idx = r * a.N + i;
+    if (STAGE == 0 && a.fresh) psi[j] = stage_noise<STAGE>(a, r, i, idx, key);
+    const StageOut o = stage_math<STAGE>(a, th_s[j], th[j], om[j], psi[j], g1[j], v[2 * j], v[2 * j + 1]);
+    stage_store<STAGE>(a, a.op_next, r, i, idx, o);
+  }
 }
 
-// D = A * B^T over K = Kdim.  EPI_STORE_D writes Dt transposed ([col][row],
-// rows contiguous) so that each column of the tile is one coalesced run;
-// the stage epilogues apply the SRK2 sub-step instead.
-// Requires M % 128 == 0, Ncols % BN == 0, Kdim % 64 == 0 (checked by the host).
 // Threads per CTA: 8 warps for the plain store, 16 for the fused stages
 // (more warps to hide the latency of the per-element SRK2 arithmetic).
 template <int EPI>
@@ -295,12 +405,44 @@ struct EpiThreads {
   static constexpr int value = EPI == EPI_STORE_D ? 256 : 512;
 };
 
+// Epilogue of one 128 x BN tile whose FP32 accumulators sit in this CTA's
+// tensor memory (lane = row, column = column): warp w reads TMEM lane
+// quarter w % 4 (the lanes it may access) and column group w / 4, then
+// stores Dt or applies the SRK2 sub-step.
+template <int BN, int EPI>
+__device__ __forceinline__ void epilogue_tile(uint32_t tmem, int m0, int n0, float *__restrict__ Dt, int M,
+                                              const StageArgs &sa) {
+  constexpr int NGROUPS = EpiThreads<EPI>::value / 128;  // column groups of the epilogue
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp & 3;       // TMEM lane quarter this warp may access
+  const int group = warp >> 2;  // which BN / NGROUPS columns
+  const int row = m0 + q * 32 + lane;
+  const uint2 key = seed_to_key(sa.seed);
+#pragma unroll 1
+  for (int cc = 0; cc < BN / NGROUPS; cc += 32) {
+    const int col = group * (BN / NGROUPS) + cc;
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
+    if (EPI == EPI_STORE_D) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Dt[(size_t)(n0 + col + i) * (size_t)M + row] = v[i];
+    } else {
+      // the chunk's 16 replicas in two groups of 8
+      stage_group<EPI == EPI_STAGE0 ? 0 : 1, 8>(sa, (int64_t)((n0 + col) / 2), (int64_t)row, v, key);
+      stage_group<EPI == EPI_STAGE0 ? 0 : 1, 8>(sa, (int64_t)((n0 + col) / 2 + 8), (int64_t)row, v + 16, key);
+    }
+  }
+}
+
+// D = A * B^T over K = Kdim.  EPI_STORE_D writes Dt transposed ([col][row],
+// rows contiguous) so that each column of the tile is one coalesced run;
+// the stage epilogues apply the SRK2 sub-step instead.
+// Requires M % 128 == 0, Ncols % BN == 0, Kdim % 64 == 0 (checked by the host).
 template <int BN, int EPI>
 __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
     tc_gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                         float *__restrict__ Dt, int M, int Kdim, uint32_t *err, const StageArgs sa,
                         uint64_t wait_ns) {
-  constexpr int NGROUPS = EpiThreads<EPI>::value / 128;  // column groups of the epilogue
   using S = Shape<BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -342,13 +484,14 @@ __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
     // ---- TMA producer ----
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+    const uint64_t pol_a = l2_evict_first_policy();
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
       if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wait_ns)) break;
       mbar_arrive_expect_tx(&full_bar[s], (uint32_t)S::STAGE_BYTES);
-      tma_load_2d(smA + s * S::A_BYTES, &mapA, &full_bar[s], kb * BK, m0);
+      tma_load_2d_hint(smA + s * S::A_BYTES, &mapA, &full_bar[s], kb * BK, m0, pol_a);
       tma_load_2d(smB + s * S::B_BYTES, &mapB, &full_bar[s], kb * BK, n0);
       issued = kb + 1;
     }
@@ -386,32 +529,164 @@ __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
   volatile int no_abort = 0;
   const bool ok = mbar_wait(&acc_bar, 0, &no_abort) && !abort_flag;
   tmem_fence_after();
-  if (ok) {
-    const int q = warp & 3;       // TMEM lane quarter this warp may access
-    const int group = warp >> 2;  // which BN / NGROUPS columns
-    const int row = m0 + q * 32 + lane;
-    const uint2 key = seed_to_key(sa.seed);
-#pragma unroll 1
-    for (int cc = 0; cc < BN / NGROUPS; cc += 32) {
-      const int col = group * (BN / NGROUPS) + cc;
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, v);
-      if (EPI == EPI_STORE_D) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) Dt[(size_t)(n0 + col + i) * (size_t)M + row] = v[i];
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          stage_element<EPI == EPI_STAGE0 ? 0 : 1>(sa, sa.op_next, (int64_t)((n0 + col) / 2 + j), (int64_t)row,
-                                                   v[2 * j], v[2 * j + 1], key);
-      }
-    }
-  }
+  if (ok) epilogue_tile<BN, EPI>(tmem, m0, n0, Dt, M, sa);
   tmem_fence_before();
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)S::TMEM_COLS)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && (abort_flag || !ok)) atomicOr(err, kErrTimeout);
+}
+
+// ---- CTA-pair GEMM (cta_group::2) --------------------------------------
+//
+// The same product with one 256 x 256 tile of D per pair of CTAs (a cluster
+// of two along M).  Each CTA stages its own 128 rows of A and 128 of the 256
+// rows of B per K slice (32 KB instead of 48 KB for 128 x 256 of D), so the
+// shared-memory writes (TMA) and reads (MMA) per FLOP fall by a third.
+//   both CTAs   : TMA producer for its own half of each slot; the bytes of
+//                 both halves complete on the even CTA's full_bar
+//   even CTA    : MMA issuer of the pair (M = 256, N = 256, K = 16 per MMA);
+//                 tcgen05.commit multicasts every slot release (empty_bar)
+//                 and the final accumulator barrier to both CTAs
+//   all warps   : epilogue of this CTA's 128 rows from its own tensor memory
+// Teardown: after the accumulator barrier a cluster barrier makes both CTAs'
+// issue counts final; where a wait expired, the even CTA completes the phase
+// of every slot loaded but not consumed (accounting for the half that was
+// never issued) and waits for it, so that no load of either CTA is in flight
+// when the final cluster barrier lets the CTAs free their tensor memory and
+// leave.
+constexpr int STAGES2 = 6;
+constexpr int BN2 = 256;       // D columns per pair (both CTAs hold all of them)
+constexpr int BH2 = BN2 / 2;   // B rows per CTA
+constexpr int A2_BYTES = BM * BK * 2;
+constexpr int B2_BYTES = BH2 * BK * 2;
+constexpr int STAGE2_BYTES = A2_BYTES + B2_BYTES;  // one CTA's half of a slot
+constexpr int SMEM2_BYTES = STAGES2 * STAGE2_BYTES + 1024;
+constexpr int TMEM2_COLS = BN2;
+
+// D = A * B^T, tile rows m0 = 128 * blockIdx.x (the pair covers 256 rows),
+// columns n0 = 256 * blockIdx.y.  mapB's box is 128 rows (half a tile).
+// Requires M % 256 == 0, Ncols % 256 == 0, Kdim % 64 == 0 (checked by the
+// host); launched with gridDim.x even (clusters of 2 along x).
+template <int EPI>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::value, 1)
+    tc_gemm2_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                         float *__restrict__ Dt, int M, int Kdim, uint32_t *err, const StageArgs sa,
+                         uint64_t wait_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *smA = smem;
+  uint8_t *smB = smem + STAGES2 * A2_BYTES;
+  __shared__ __align__(8) uint64_t full_bar[STAGES2];   // even CTA: both halves of the slot landed
+  __shared__ __align__(8) uint64_t empty_bar[STAGES2];  // the pair's MMAs of the slot completed
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int issued_cnt;    // K slices whose loads this CTA issued
+  __shared__ int consumed_cnt;  // even CTA: K slices whose MMAs were issued
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN2;
+  const int nk = Kdim / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES2; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&acc_bar, 1);
+    abort_flag = 0;
+    issued_cnt = 0;
+    consumed_cnt = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    // one warp of each CTA of the pair allocates, together, the same columns
+    // of both CTAs' tensor memory
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"((uint32_t)TMEM2_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tmem_fence_before();
+  cluster_barrier();  // both CTAs' barriers initialised, tensor memory allocated
+  tmem_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer (both CTAs, each its own half) ----
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+    const int b_row = n0 + (int)rank * BH2;
+    const uint64_t pol_a = l2_evict_first_policy();
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES2;
+      const uint32_t ph = (uint32_t)(kb / STAGES2) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wait_ns)) break;
+      if (rank == 0) mbar_arrive_expect_tx(&full_bar[s], 2u * (uint32_t)STAGE2_BYTES);
+      const uint32_t fb = mapa_shared(&full_bar[s], 0);
+      tma_load_2d_pair_hint(smA + s * A2_BYTES, &mapA, fb, kb * BK, m0, pol_a);
+      tma_load_2d_pair(smB + s * B2_BYTES, &mapB, fb, kb * BK, b_row);
+      issued = kb + 1;
+    }
+    issued_cnt = issued;
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---- MMA issuer of the pair ----
+    constexpr uint32_t idesc = idesc_bf16_f32(2 * BM, BN2);
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = kb % STAGES2;
+      const uint32_t ph = (uint32_t)(kb / STAGES2) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag, wait_ns)) break;
+      tmem_fence_after();
+      const uint64_t adesc = smem_desc_sw128(smA + s * A2_BYTES);
+      const uint64_t bdesc = smem_desc_sw128(smB + s * B2_BYTES);
+#pragma unroll
+      for (int k = 0; k < BK / UMMA_K; ++k)
+        umma_bf16_pair(tmem, adesc + (uint64_t)(k * UMMA_K * 2 / 16), bdesc + (uint64_t)(k * UMMA_K * 2 / 16),
+                       idesc, (kb | k) != 0 ? 1u : 0u);
+      umma_commit_pair(&empty_bar[s]);
+    }
+    consumed_cnt = kb;
+    umma_commit_pair(&acc_bar);  // arrives in both CTAs when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  volatile int no_abort = 0;
+  const bool acc_ok = mbar_wait(&acc_bar, 0, &no_abort);
+  cluster_barrier();  // issue counts, the consumed count and both abort flags are final
+  const bool ok = acc_ok && !abort_flag && !ld_shared_cluster_s32(mapa_shared(&abort_flag, rank ^ 1u));
+  if (rank == 0 && threadIdx.x == 0) {
+    // Slots loaded but not consumed (after an expired wait only): at most
+    // STAGES2 consecutive K slices, one per slot, each the slot's pending
+    // phase.  A half issued by one CTA only: count the other half as done
+    // (or make the arrival the even CTA never made), then wait for the phase.
+    const int own = issued_cnt, peer = ld_shared_cluster_s32(mapa_shared(&issued_cnt, 1u));
+    const int hi = own > peer ? own : peer;
+    volatile int no_abort2 = 0;
+    for (int kb = consumed_cnt; kb < hi; ++kb) {
+      const int s = kb % STAGES2;
+      if (kb < own && kb >= peer) mbar_complete_tx(&full_bar[s], (uint32_t)STAGE2_BYTES);
+      if (kb >= own && kb < peer) mbar_arrive_expect_tx(&full_bar[s], (uint32_t)STAGE2_BYTES);
+      mbar_wait(&full_bar[s], (uint32_t)(kb / STAGES2) & 1u, &no_abort2);
+    }
+  }
+  // ---- epilogue: all warps of both CTAs, each CTA its own 128 rows ----
+  tmem_fence_after();
+  if (ok) epilogue_tile<BN2, EPI>(tmem, m0, n0, Dt, M, sa);
+  tmem_fence_before();
+  // neither CTA frees the pair's tensor memory or leaves (with its barriers
+  // and shared memory) while the other, or a load, may still use them
+  cluster_barrier();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM2_COLS)
                  : "memory");
   }
   if (threadIdx.x == 0 && (abort_flag || !ok)) atomicOr(err, kErrTimeout);

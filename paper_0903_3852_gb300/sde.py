@@ -33,6 +33,7 @@ SDE_FLAG_TIME_KERNELS = 2
 SDE_FLAG_FUSED = 4
 SDE_FLAG_EULER = 8
 SDE_FLAG_ASYNC_EXCHANGE = 16
+SDE_FLAG_GEMM_SINGLE_CTA = 32
 
 
 class SDEError(RuntimeError):

@@ -1,6 +1,7 @@
 """Failure detection on the GPU without a GPU fault.
 
-- Bounded device waits: the tensor-core GEMM (its TMA producer and MMA issuer)
+- Bounded device waits: the tensor-core GEMMs (the TMA producers, the MMA
+  issuer and, in the CTA-pair GEMM, the odd CTA's relay)
   and the Kuramoto mean field with the asynchronous cluster exchange wait on
   mbarriers with a limit of the GPU's nanosecond timer.  A limit of 1 ns makes
   those waits expire on purpose: the kernels drain what they issued, latch
@@ -25,14 +26,16 @@ def _general(N, R, seed):
     return sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, seed, sample_every=10)
 
 
-def test_tensor_core_gemm_wait_expiry_is_reported_and_recovered():
-    N, R, steps = 512, 64, 20
+@pytest.mark.parametrize("N,R,cluster", [(512, 64, 1), (1024, 128, 2)])  # one-CTA GEMM, CTA-pair GEMM
+def test_tensor_core_gemm_wait_expiry_is_reported_and_recovered(N, R, cluster):
+    steps = 20
     w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=31)
     K = torch.from_numpy(w["Kmat"]).cuda()
     ref = _general(N, R, 3)
     ref.set_coupling(K)
     phi_ref, r_ref, _ = kur_run(ref, w["phi0"], w["omega"], 0, steps)
     ens = _general(N, R, 3)
+    assert ens.tuning()[2] == cluster
     ens.set_coupling(K)
     ens.set_wait_limit(1)
     with pytest.raises(sde.SDEError) as e:

@@ -10,6 +10,9 @@
   of the FP64 oracle's r(t) over the same replicas and noise.
 - Full size (N = 8192, 256 replicas): sampled coupling rows against the FP64
   direct sum.
+- The CTA-pair GEMM (256 x 256 tile per cluster of two CTAs, tcgen05
+  cta_group::2, the default where the sizes allow) against the one-CTA GEMM:
+  the same coupling sums and trajectories bit for bit.
 """
 import math
 
@@ -150,3 +153,26 @@ def test_fused_epilogue_equals_separate_stage_kernels():
         outs.append(kur_run(ens, w["phi0"], w["omega"], 0, steps))
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("N,R", [(1024, 128), (768, 256)])
+def test_cta_pair_gemm_equals_single_cta_gemm(N, R):
+    # each element of D is accumulated over the same K slices in the same
+    # order by both GEMMs; only the tiling over CTAs differs
+    steps = 25
+    w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=14)
+    K = torch.from_numpy(w["Kmat"]).cuda()
+    phi = torch.from_numpy(w["phi0"]).cuda()
+    sums, runs = [], []
+    for flags in (0, sde.SDE_FLAG_GEMM_SINGLE_CTA):
+        ensure_built()
+        ens = sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, 4, sample_every=5,
+                                    flags=flags)
+        assert ens.tuning()[2] == (1 if flags else 2)
+        ens.set_coupling(K)
+        sums.append(ens.coupling(phi).cpu().numpy())
+        runs.append(kur_run(ens, w["phi0"], w["omega"], 0, steps))
+    print("pair vs single CTA: max |d sum| %.3e, max |d phi| %.3e"
+          % (np.abs(sums[0] - sums[1]).max(), np.abs(runs[0][0] - runs[1][0]).max()))
+    assert np.array_equal(sums[0], sums[1])
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
