@@ -88,8 +88,10 @@ def parse():
                     help="general coupling, tensor-core form: SRK2 sub-steps as separate kernels instead of "
                          "in the GEMM epilogue (the default)")
     ap.add_argument("--gemm-single-cta", action="store_true",
-                    help="general coupling, tensor-core form: one CTA per 128 x 256 GEMM tile instead of "
-                         "the CTA-pair GEMM (256 x 256 per cluster of two CTAs)")
+                    help="general coupling, tensor-core form: whole tiles, one CTA per 128 x 256 GEMM tile")
+    ap.add_argument("--gemm-stream-k", action="store_true",
+                    help="general coupling, tensor-core form: split the K range of all tiles over every "
+                         "resident CTA (stream-K) instead of whole tiles")
     return ap.parse_args()
 
 
@@ -435,7 +437,8 @@ def run_ours(args, rank, world, device):
         N, R = w["n_osc"], w["replicas"]
         fused = tc and not args.separate_stage
         flags = (sde.SDE_FLAG_TIME_KERNELS | (sde.SDE_FLAG_FUSED if fused else 0)
-                 | (sde.SDE_FLAG_GEMM_SINGLE_CTA if args.gemm_single_cta else 0))
+                 | (sde.SDE_FLAG_GEMM_SINGLE_CTA if args.gemm_single_cta else 0)
+                 | (sde.SDE_FLAG_GEMM_STREAM_K if args.gemm_stream_k else 0))
         ens = sde.Ensemble.kuramoto(model, N, R, 0.0, w["D"], w["dt"], w["seed"],
                                     sample_every=w["sample_every"], flags=flags)
         Kdev = torch.from_numpy(w["Kmat"]).to(device)
@@ -459,12 +462,16 @@ def run_ours(args, rank, world, device):
         units = float(N * R * S)
         metric = "oscillator-steps/sec"
         flop_per_launch = 2.0 * N * (2 * R) * N  # one GEMM K . [sin | cos]
-        launches_per_step = 4 * S + S // w["sample_every"] + 4
+        # per step two GEMMs (+ two stage kernels unless fused); r(t) samples;
+        # the operand kernel, the last sample and the flush
+        launches_per_step = (2 if fused else 4) * S + S // w["sample_every"] + 4
         cfg = {"workload": kuramoto_workload_name(args.workload, False, N, R),
                "stage": "fused into the GEMM epilogue" if fused else "separate kernel",
                "steps_per_bench_step": S, "K0": w["K0"], "D": w["D"], "dt": w["dt"],
                "gemm": "M=%d N=%d K=%d per stage, 2 per step" % (N, 2 * R, N),
-               "gemm_tiling": ({2: "256 x 256 per CTA pair (tcgen05 cta_group::2)",
+               "gemm_tiling": ({0: "stream-K: 128 x 256 tiles, K split over %d CTAs (tcgen05 cta_group::1)"
+                                   % ens.tuning()[1],
+                                2: "256 x 256 per CTA pair (tcgen05 cta_group::2)",
                                 1: "128 x %d per CTA (tcgen05 cta_group::1)" % ens.tuning()[1]}[ens.tuning()[2]]
                                if tc else "128 x 128 per CTA (FP32 FMA)"),
                "l2": "K matrix %d MiB streams each GEMM; flushed between steps (256 MiB write)"

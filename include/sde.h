@@ -72,7 +72,10 @@ typedef enum sde_schedule {
 /* Flags for sde_config.flags. */
 #define SDE_FLAG_NO_GRAPH 1u     /* launch kernels directly instead of replaying a graph */
 #define SDE_FLAG_TIME_KERNELS 2u /* Kuramoto pairwise / general: CUDA events around every
-                                    launch of the dominant kernel (stage / GEMM) */
+                                    launch of the dominant kernel (stage / GEMM); for the
+                                    general coupling around the GEMMs of every 8th step only
+                                    (events between back-to-back GEMMs keep the next one's
+                                    prologue from overlapping the previous one's end) */
 #define SDE_FLAG_FUSED 4u        /* general coupling, tensor-core form: run the SRK2
                                     sub-steps in the GEMM epilogue instead of as
                                     separate kernels (same results bit for bit) */
@@ -80,11 +83,21 @@ typedef enum sde_schedule {
                                         by asynchronous remote stores that complete on the
                                         receiving CTA's mbarrier, instead of a cluster barrier
                                         (the autotuner tries both forms when unset) */
-#define SDE_FLAG_GEMM_SINGLE_CTA 32u /* general coupling, tensor-core form: one CTA per 128 x 256
-                                        tile of the GEMM (tcgen05 cta_group::1) instead of the
-                                        CTA-pair GEMM (a 256 x 256 tile per cluster of two CTAs,
-                                        cta_group::2) that runs by default where n_osc % 256 == 0
-                                        and n_replicas % 128 == 0 (same results bit for bit) */
+#define SDE_FLAG_GEMM_SINGLE_CTA 32u /* general coupling, tensor-core form: whole tiles, one CTA
+                                        per 128 x 256 tile of the GEMM (tcgen05 cta_group::1),
+                                        instead of the CTA-pair GEMM (a 256 x 256 tile per
+                                        cluster of two CTAs, cta_group::2) that whole tiles use by
+                                        default where n_osc % 256 == 0 and n_replicas % 128 == 0
+                                        (same results bit for bit) */
+#define SDE_FLAG_GEMM_STREAM_K 64u /* general coupling, tensor-core form (n_replicas % 128 == 0):
+                                      split the K range of all 128 x 256 tiles evenly over as many
+                                      CTAs as can be resident (stream-K); each tile's first CTA
+                                      adds the others' FP32 partial sums (equal to the whole-tile
+                                      GEMM up to the rounding of those sums, deterministic on a
+                                      given GPU).  A split K slice costs about 1.4 times a
+                                      whole-tile one, so this pays only where whole tiles fill
+                                      few SMs and K is long (N = 8192 with 128 replicas: 9 %
+                                      faster); not at N = 8192 with 256 replicas */
 #define SDE_FLAG_EULER 8u        /* Euler-Maruyama instead of SRK2 (Alg. 2): the
                                     first-order scheme of PROG2 (Sec. 4.2).
                                     Josephson: every schedule, same kernels with
@@ -259,8 +272,10 @@ const char *sde_last_error(void);
    cluster of the mean-field kernel; 0 for the grid-wide mean field, whose
    per-thread count is then the oscillators each thread strides over; for the
    general coupling's tensor-core GEMM, the CTAs per tile: 2 for the CTA-pair
-   GEMM, whose per-thread value is then the D columns of a tile; 1
-   otherwise).  Any pointer may be NULL. */
+   GEMM, whose per-thread value is then the D columns of a tile, 0 for the
+   stream-K split (SDE_FLAG_GEMM_STREAM_K), whose per-thread value is then
+   the CTAs of the split grid;
+   1 otherwise).  Any pointer may be NULL. */
 sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads, int32_t *per_thread,
                           int32_t *cluster_ctas);
 
@@ -268,8 +283,9 @@ sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads, int32_t *p
  * Device time of the dominant kernel of the last run, from CUDA events
  * recorded on the run's stream around it: the persistent or per-point
  * Josephson launches, the mean-field kernel, or -- with
- * SDE_FLAG_TIME_KERNELS -- each pairwise stage / GEMM launch (mean_ms per
- * launch, total_ms summed, launches counted).  Without that flag the
+ * SDE_FLAG_TIME_KERNELS -- each pairwise stage launch or each GEMM launch of
+ * every 8th step (mean_ms per timed launch, total_ms summed over them,
+ * launches = the timed launches).  Without that flag the
  * Kuramoto loop is bracketed as one launch.  Synchronises that stream.
  * sde_last_kernel_ms returns mean_ms.
  */

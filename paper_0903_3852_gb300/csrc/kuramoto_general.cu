@@ -22,11 +22,13 @@
 
 #include <algorithm>
 #include <string>
+#include <utility>
 
 #include "kuramoto.h"
 #include "kuramoto_internal.h"
 #include "philox.cuh"
 #include "tc_gemm.cuh"
+#include "tc_gemm_sk.cuh"
 #include "tma_map.h"
 
 namespace sde {
@@ -195,6 +197,8 @@ __global__ void __launch_bounds__(256) sgemm_nt_kernel(const float *__restrict__
   }
 }
 
+constexpr int64_t kTimedStepStride = 8;
+
 int grid_for(int64_t n, int sm_count) {
   const int64_t b = (n + 255) / 256;
   return (int)std::min<int64_t>(b, (int64_t)sm_count * 16);
@@ -211,6 +215,11 @@ struct GemmPlan {
   CUtensorMap mapOpHalf[2];  // box of 128 rows (one CTA's half of a pair tile)
   int bn = 0;
   bool pair = false;  // CTA-pair GEMM (tc_gemm2_bf16_kernel)
+  // stream-K GEMM (tc_gemm_sk_bf16_kernel): sk_P CTAs, 0 = whole tiles
+  int sk_P = 0;
+  float *ws = nullptr;        // [sk_P][256][128] partial sums
+  uint32_t *flags = nullptr;  // [sk_P] epoch of the partial in each slot
+  uint32_t epoch = 0;
 };
 
 bool is_tc(const KuramotoCtx *k) { return k->model == SDE_KURAMOTO_GENERAL; }
@@ -241,22 +250,55 @@ tc::StageArgs stage_args(KuramotoCtx *k, int next, const float *omega, int64_t n
   return a;
 }
 
+// Launch with programmatic stream serialization: the GEMM's prologue
+// (barrier set-up, tensor-memory allocation) may start while the previous
+// kernel of the stream finishes; the kernel waits (griddepcontrol.wait)
+// before it reads anything that kernel wrote.
+template <typename... Params, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, int threads, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <int BN, int EPI>
-void launch_tc(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
+cudaError_t launch_tc(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
   GemmPlan *g = (GemmPlan *)k->gemm_plan;
   const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
-  dim3 grid(M / tc::BM, Ncols / BN);
-  tc::tc_gemm_bf16_kernel<BN, EPI><<<grid, tc::EpiThreads<EPI>::value, tc::Shape<BN>::SMEM_BYTES, s>>>(
-      g->mapK, g->mapOp[which], k->P, M, Kdim, k->err, sa, k->wait_ns);
+  return launch_dependent(tc::tc_gemm_bf16_kernel<BN, EPI>, dim3(M / tc::BM, Ncols / BN), tc::EpiThreads<EPI>::value,
+                          tc::Shape<BN>::SMEM_BYTES, s, g->mapK, g->mapOp[which], k->P, M, Kdim, k->err, sa,
+                          k->wait_ns);
 }
 
 template <int EPI>
-void launch_tc2(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
+cudaError_t launch_tc2(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
   GemmPlan *g = (GemmPlan *)k->gemm_plan;
   const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
-  dim3 grid(M / tc::BM, Ncols / tc::BN2);  // clusters of two CTAs along x
-  tc::tc_gemm2_bf16_kernel<EPI><<<grid, tc::EpiThreads<EPI>::value, tc::SMEM2_BYTES, s>>>(
-      g->mapK, g->mapOpHalf[which], k->P, M, Kdim, k->err, sa, k->wait_ns);
+  // clusters of two CTAs along x (the kernel's compile-time cluster shape)
+  return launch_dependent(tc::tc_gemm2_bf16_kernel<EPI>, dim3(M / tc::BM, Ncols / tc::BN2),
+                          tc::EpiThreads<EPI>::value, tc::SMEM2_BYTES, s, g->mapK, g->mapOpHalf[which], k->P, M,
+                          Kdim, k->err, sa, k->wait_ns);
+}
+
+template <int EPI>
+cudaError_t launch_sk(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaStream_t s) {
+  GemmPlan *g = (GemmPlan *)k->gemm_plan;
+  const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
+  const int tiles_n = Ncols / tc::SK_BN;
+  const int64_t T = (int64_t)(M / tc::BM) * tiles_n * (Kdim / tc::BK);
+  if (++g->epoch == 0) g->epoch = 1;  // flags start at 0: epoch 0 never marks a partial
+  return launch_dependent(tc::tc_gemm_sk_bf16_kernel<EPI>, dim3((unsigned)g->sk_P), tc::SK_THREADS,
+                          tc::SK_SMEM_BYTES, s, g->mapK, g->mapOp[which], k->P, M, Kdim, tiles_n, T, g->ws,
+                          g->flags, g->epoch, k->err, sa, k->wait_ns);
 }
 
 // GEMM reading operand buffer `which`; epi = EPI_STORE_D writes Dt, the stage
@@ -267,19 +309,24 @@ cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s, int epi = tc:
   if (is_tc(k)) {
     GemmPlan *g = (GemmPlan *)k->gemm_plan;
     const tc::StageArgs sa = stage_args(k, epi == tc::EPI_STORE_D ? -1 : 1 - which, omega, n, run_begin);
-    if (g->pair) {
-      if (epi == tc::EPI_STAGE0) launch_tc2<tc::EPI_STAGE0>(k, which, sa, s);
-      else if (epi == tc::EPI_STAGE1) launch_tc2<tc::EPI_STAGE1>(k, which, sa, s);
-      else launch_tc2<tc::EPI_STORE_D>(k, which, sa, s);
-    } else if (g->bn == 256) {
-      if (epi == tc::EPI_STAGE0) launch_tc<256, tc::EPI_STAGE0>(k, which, sa, s);
-      else if (epi == tc::EPI_STAGE1) launch_tc<256, tc::EPI_STAGE1>(k, which, sa, s);
-      else launch_tc<256, tc::EPI_STORE_D>(k, which, sa, s);
-    } else {
-      if (epi == tc::EPI_STAGE0) launch_tc<128, tc::EPI_STAGE0>(k, which, sa, s);
-      else if (epi == tc::EPI_STAGE1) launch_tc<128, tc::EPI_STAGE1>(k, which, sa, s);
-      else launch_tc<128, tc::EPI_STORE_D>(k, which, sa, s);
+    if (g->sk_P > 0) {
+      if (epi == tc::EPI_STAGE0) return launch_sk<tc::EPI_STAGE0>(k, which, sa, s);
+      if (epi == tc::EPI_STAGE1) return launch_sk<tc::EPI_STAGE1>(k, which, sa, s);
+      return launch_sk<tc::EPI_STORE_D>(k, which, sa, s);
     }
+    if (g->pair) {
+      if (epi == tc::EPI_STAGE0) return launch_tc2<tc::EPI_STAGE0>(k, which, sa, s);
+      if (epi == tc::EPI_STAGE1) return launch_tc2<tc::EPI_STAGE1>(k, which, sa, s);
+      return launch_tc2<tc::EPI_STORE_D>(k, which, sa, s);
+    }
+    if (g->bn == 256) {
+      if (epi == tc::EPI_STAGE0) return launch_tc<256, tc::EPI_STAGE0>(k, which, sa, s);
+      if (epi == tc::EPI_STAGE1) return launch_tc<256, tc::EPI_STAGE1>(k, which, sa, s);
+      return launch_tc<256, tc::EPI_STORE_D>(k, which, sa, s);
+    }
+    if (epi == tc::EPI_STAGE0) return launch_tc<128, tc::EPI_STAGE0>(k, which, sa, s);
+    if (epi == tc::EPI_STAGE1) return launch_tc<128, tc::EPI_STAGE1>(k, which, sa, s);
+    return launch_tc<128, tc::EPI_STORE_D>(k, which, sa, s);
   } else {
     dim3 grid((M + SG_BM - 1) / SG_BM, (Ncols + SG_BN - 1) / SG_BN);
     sgemm_nt_kernel<<<grid, 256, 0, s>>>(k->Kf32, (const float *)op_buf(k, which), k->P, M, Ncols, Kdim);
@@ -367,13 +414,51 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
       if ((e = cudaFuncSetAttribute(kernels2[q], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     tc::SMEM2_BYTES)) != cudaSuccess)
         return cuda_fail(e, "cudaFuncSetAttribute");
+    // Stream-K on request (SDE_FLAG_GEMM_STREAM_K): as many CTAs as can be
+    // resident at once (every CTA must be, for the heads' waits to end), each
+    // with at least SK_MIN_UNITS K slices, where that is more CTAs than tiles.
+    if (g->bn == 256 && (k->flags & SDE_FLAG_GEMM_STREAM_K)) {
+      const void *kernels3[] = {(const void *)tc::tc_gemm_sk_bf16_kernel<tc::EPI_STORE_D>,
+                                (const void *)tc::tc_gemm_sk_bf16_kernel<tc::EPI_STAGE0>,
+                                (const void *)tc::tc_gemm_sk_bf16_kernel<tc::EPI_STAGE1>};
+      int resident = 1 << 30;
+      for (int q = 0; q < 3; ++q) {
+        if ((e = cudaFuncSetAttribute(kernels3[q], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc::SK_SMEM_BYTES)) != cudaSuccess)
+          return cuda_fail(e, "cudaFuncSetAttribute");
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernels3[q], tc::SK_THREADS,
+                                                               tc::SK_SMEM_BYTES)) != cudaSuccess)
+          return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        resident = std::min(resident, per_sm * k->sm_count);
+      }
+      const int64_t tiles = (k->N / tc::BM) * (2 * k->R / tc::SK_BN);
+      const int64_t T = tiles * (k->N / tc::BK);
+      const int64_t P = std::min<int64_t>(resident, T / tc::SK_MIN_UNITS);
+      if (P > tiles) {
+        g->sk_P = (int)P;
+        if ((e = device_alloc((void **)&g->ws, (size_t)P * tc::SK_BN * tc::BM * sizeof(float))) != cudaSuccess)
+          return cuda_fail(e, "cudaMalloc");
+        if ((e = device_alloc((void **)&g->flags, (size_t)P * sizeof(uint32_t))) != cudaSuccess)
+          return cuda_fail(e, "cudaMalloc");
+        if ((e = cudaMemset(g->flags, 0, (size_t)P * sizeof(uint32_t))) != cudaSuccess)
+          return cuda_fail(e, "cudaMemset");
+      }
+    }
   } else {
     if ((e = device_alloc((void **)&k->Kf32, NN * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = device_alloc((void **)&k->Bt32, NR * 2 * 4 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   }
   k->block = is_tc(k) ? tc::THREADS : 256;
   k->opt = is_tc(k) ? ((GemmPlan *)k->gemm_plan)->bn : SG_BN;
-  k->cs = (is_tc(k) && ((GemmPlan *)k->gemm_plan)->pair) ? 2 : 1;  // CTAs per GEMM tile
+  if (is_tc(k)) {
+    const GemmPlan *g = (const GemmPlan *)k->gemm_plan;
+    // CTAs per GEMM tile (0: stream-K, the split grid's CTA count in opt)
+    k->cs = g->sk_P > 0 ? 0 : (g->pair ? 2 : 1);
+    if (g->sk_P > 0) k->opt = g->sk_P;
+  } else {
+    k->cs = 1;
+  }
   return SDE_OK;
 }
 
@@ -384,6 +469,10 @@ void kuramoto_general_free(KuramotoCtx *k) {
   cudaFree(k->Bt32);
   cudaFree(k->P);
   cudaFree(k->psi4);
+  if (k->gemm_plan) {
+    cudaFree(((GemmPlan *)k->gemm_plan)->ws);
+    cudaFree(((GemmPlan *)k->gemm_plan)->flags);
+  }
   delete (GemmPlan *)k->gemm_plan;
   k->gemm_plan = nullptr;
 }
@@ -417,23 +506,27 @@ sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStrea
       SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
       ++sample;
     }
+    // GEMM launches are timed (SDE_FLAG_TIME_KERNELS) on every
+    // kTimedStepStride-th step only: an event between two GEMMs keeps the
+    // second one's prologue from overlapping the first one's end
+    const bool timed = (n - r->n_begin) % kTimedStepStride == 0;
     if (is_tc(k) && (k->flags & SDE_FLAG_FUSED)) {
       // the SRK2 sub-steps run in the GEMM epilogues
-      SDE_CUDA_TRY(ktime_begin(k, s));
+      if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
       SDE_CUDA_TRY(launch_gemm(k, 0, s, tc::EPI_STAGE0, r->omega_dev, n, r->n_begin));
-      SDE_CUDA_TRY(ktime_end(k, s));
-      SDE_CUDA_TRY(ktime_begin(k, s));
+      if (timed) SDE_CUDA_TRY(ktime_end(k, s));
+      if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
       SDE_CUDA_TRY(launch_gemm(k, 1, s, tc::EPI_STAGE1, r->omega_dev, n, r->n_begin));
-      SDE_CUDA_TRY(ktime_end(k, s));
+      if (timed) SDE_CUDA_TRY(ktime_end(k, s));
       continue;
     }
-    SDE_CUDA_TRY(ktime_begin(k, s));
+    if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 0, s));
-    SDE_CUDA_TRY(ktime_end(k, s));
+    if (timed) SDE_CUDA_TRY(ktime_end(k, s));
     SDE_CUDA_TRY(launch_stage<0>(k, 1, r->omega_dev, n, r->n_begin, s));
-    SDE_CUDA_TRY(ktime_begin(k, s));
+    if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 1, s));
-    SDE_CUDA_TRY(ktime_end(k, s));
+    if (timed) SDE_CUDA_TRY(ktime_end(k, s));
     SDE_CUDA_TRY(launch_stage<1>(k, 0, r->omega_dev, n, r->n_begin, s));
   }
   if (k->M > 0) SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));

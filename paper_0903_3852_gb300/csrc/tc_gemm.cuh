@@ -137,6 +137,14 @@ __device__ __forceinline__ int ld_shared_cluster_s32(uint32_t addr) {
   return v;
 }
 
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed and their memory is visible (a no-op for a plain launch),
+// and let the next grid of the stream start its own prologue on free SMs.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -479,6 +487,10 @@ __global__ void __launch_bounds__(EpiThreads<EPI>::value, 1)
   __syncthreads();
   tmem_fence_after();
   const uint32_t tmem = tmem_slot;
+  // everything above overlaps the previous kernel of the stream (programmatic
+  // dependent launch); the operand and the SRK2 state are read only below
+  griddep_wait();
+  griddep_launch_dependents();
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
@@ -618,6 +630,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
   cluster_barrier();  // both CTAs' barriers initialised, tensor memory allocated
   tmem_fence_after();
   const uint32_t tmem = tmem_slot;
+  griddep_wait();  // as in the one-CTA kernel
+  griddep_launch_dependents();
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer (both CTAs, each its own half) ----

@@ -34,6 +34,7 @@ SDE_FLAG_FUSED = 4
 SDE_FLAG_EULER = 8
 SDE_FLAG_ASYNC_EXCHANGE = 16
 SDE_FLAG_GEMM_SINGLE_CTA = 32
+SDE_FLAG_GEMM_STREAM_K = 64
 
 
 class SDEError(RuntimeError):

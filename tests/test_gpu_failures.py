@@ -1,7 +1,7 @@
 """Failure detection on the GPU without a GPU fault.
 
 - Bounded device waits: the tensor-core GEMMs (the TMA producers, the MMA
-  issuer and, in the CTA-pair GEMM, the odd CTA's relay)
+  issuers, the stream-K heads' polls of their partial sums' flags)
   and the Kuramoto mean field with the asynchronous cluster exchange wait on
   mbarriers with a limit of the GPU's nanosecond timer.  A limit of 1 ns makes
   those waits expire on purpose: the kernels drain what they issued, latch
@@ -21,20 +21,23 @@ from paper_0903_3852_gb300 import inputs, sde
 pytestmark = pytest.mark.gpu
 
 
-def _general(N, R, seed):
+def _general(N, R, seed, flags=0):
     ensure_built()
-    return sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, seed, sample_every=10)
+    return sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, seed, sample_every=10,
+                                 flags=flags)
 
 
-@pytest.mark.parametrize("N,R,cluster", [(512, 64, 1), (1024, 128, 2)])  # one-CTA GEMM, CTA-pair GEMM
+# one-CTA GEMM, CTA-pair GEMM, stream-K GEMM (its heads' flag polls expire too)
+@pytest.mark.parametrize("N,R,cluster", [(512, 64, 1), (1024, 128, 2), (2048, 128, 0)])
 def test_tensor_core_gemm_wait_expiry_is_reported_and_recovered(N, R, cluster):
     steps = 20
+    flags = sde.SDE_FLAG_GEMM_STREAM_K if cluster == 0 else 0
     w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=31)
     K = torch.from_numpy(w["Kmat"]).cuda()
-    ref = _general(N, R, 3)
+    ref = _general(N, R, 3, flags)
     ref.set_coupling(K)
     phi_ref, r_ref, _ = kur_run(ref, w["phi0"], w["omega"], 0, steps)
-    ens = _general(N, R, 3)
+    ens = _general(N, R, 3, flags)
     assert ens.tuning()[2] == cluster
     ens.set_coupling(K)
     ens.set_wait_limit(1)

@@ -11,8 +11,14 @@
 - Full size (N = 8192, 256 replicas): sampled coupling rows against the FP64
   direct sum.
 - The CTA-pair GEMM (256 x 256 tile per cluster of two CTAs, tcgen05
-  cta_group::2, the default where the sizes allow) against the one-CTA GEMM:
-  the same coupling sums and trajectories bit for bit.
+  cta_group::2, the default for whole tiles where the sizes allow) against
+  the one-CTA GEMM: the same coupling sums and trajectories bit for bit.
+- The stream-K GEMM (SDE_FLAG_GEMM_STREAM_K: the K range of all tiles split
+  over every resident CTA) against the whole-tile GEMM:
+  each coupling sum differs only by the FP32 rounding of the partial sums
+  (at most one rounding of the running sum per K slice of 64, 2^-24 of
+  sum_j |K_ij| each: below 2^-14 sum_j |K_ij| for up to 1024 slices), and both
+  stay within the BF16 bound of the FP64 definition.
 """
 import math
 
@@ -139,16 +145,18 @@ def test_size_validation():
         ens.run_kuramoto(0, 1, phi, torch.empty_like(phi), phi)
 
 
-def test_fused_epilogue_equals_separate_stage_kernels():
+@pytest.mark.parametrize("N,R,gemm", [(1024, 128, 0), (2048, 128, sde.SDE_FLAG_GEMM_STREAM_K)])
+def test_fused_epilogue_equals_separate_stage_kernels(N, R, gemm):
     # the SRK2 sub-step in the GEMM epilogue computes the same expression on
     # the same FP32 accumulators as the separate stage kernels: bit-identical
-    N, R, steps = 1024, 128, 37
+    steps = 37
     w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=12)
     outs = []
     for flags in (sde.SDE_FLAG_FUSED, 0):
         ensure_built()
         ens = sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, 4, sample_every=10,
-                                    flags=flags)
+                                    flags=flags | gemm)
+        assert ens.tuning()[2] == (0 if gemm else 2)
         ens.set_coupling(torch.from_numpy(w["Kmat"]).cuda())
         outs.append(kur_run(ens, w["phi0"], w["omega"], 0, steps))
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -176,3 +184,36 @@ def test_cta_pair_gemm_equals_single_cta_gemm(N, R):
           % (np.abs(sums[0] - sums[1]).max(), np.abs(runs[0][0] - runs[1][0]).max()))
     assert np.array_equal(sums[0], sums[1])
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("N,R", [(2048, 128), (4096, 128)])  # tiles split in 2 and in 4
+def test_stream_k_gemm_matches_whole_tiles(N, R):
+    steps = 20
+    w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=15)
+    K = torch.from_numpy(w["Kmat"]).cuda()
+    phi = torch.from_numpy(w["phi0"]).cuda()
+    sums, runs = {}, {}
+    SK = sde.SDE_FLAG_GEMM_STREAM_K
+    for flags in (SK, 0):
+        ensure_built()
+        ens = sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, 4, sample_every=5,
+                                    flags=flags)
+        if flags == SK:
+            tiles = (N // 128) * (2 * R // 256)
+            assert ens.tuning()[2] == 0 and ens.tuning()[1] > tiles  # stream-K over more CTAs than tiles
+        else:
+            assert ens.tuning()[2] == 2
+        ens.set_coupling(K)
+        sums[flags] = ens.coupling(phi).cpu().numpy().astype(np.float64)
+        runs[flags] = kur_run(ens, w["phi0"], w["omega"], 0, steps)
+    absK = np.abs(w["Kmat"].astype(np.float64)).sum(axis=1)[None, :]
+    d = np.abs(sums[SK] - sums[0])
+    rows = list(range(0, 128, 5)) + list(range(N - 128, N, 11))
+    ref = _direct_rows(w["phi0"], w["Kmat"], rows)
+    dphi = np.abs(angle_diff(runs[SK][0], runs[0][0]))
+    print("stream-K vs whole tiles N=%d: max |d sum| / sum|K| %.3e, max |d phi| %.3e, max err vs FP64 %.3e"
+          % (N, (d / absK).max(), dphi.max(), np.abs(sums[SK][:, rows] - ref).max()))
+    assert np.all(d <= 2.0 ** -14 * absK)
+    assert np.all(np.abs(sums[SK][:, rows] - ref) <= 2.0 ** -7 * absK[:, rows])
+    assert dphi.max() <= 1e-5
+    assert np.abs(runs[SK][1] - runs[0][1]).max() <= 1e-6
