@@ -73,9 +73,10 @@ typedef enum sde_schedule {
 #define SDE_FLAG_NO_GRAPH 1u     /* launch kernels directly instead of replaying a graph */
 #define SDE_FLAG_TIME_KERNELS 2u /* Kuramoto pairwise / general: CUDA events around every
                                     launch of the dominant kernel (stage / GEMM); for the
-                                    general coupling around the GEMMs of every 8th step only
-                                    (events between back-to-back GEMMs keep the next one's
-                                    prologue from overlapping the previous one's end) */
+                                    general coupling around the GEMMs of every 8th step only,
+                                    or with SDE_FLAG_FUSED around the whole run of back-to-back
+                                    GEMMs (events between GEMMs keep the next one's prologue
+                                    from overlapping the previous one's end) */
 #define SDE_FLAG_FUSED 4u        /* general coupling, tensor-core form: run the SRK2
                                     sub-steps in the GEMM epilogue instead of as
                                     separate kernels (same results bit for bit) */
@@ -283,9 +284,10 @@ sde_status sde_get_tuning(const sde_ctx *ctx, int32_t *block_threads, int32_t *p
  * Device time of the dominant kernel of the last run, from CUDA events
  * recorded on the run's stream around it: the persistent or per-point
  * Josephson launches, the mean-field kernel, or -- with
- * SDE_FLAG_TIME_KERNELS -- each pairwise stage launch or each GEMM launch of
- * every 8th step (mean_ms per timed launch, total_ms summed over them,
- * launches = the timed launches).  Without that flag the
+ * SDE_FLAG_TIME_KERNELS -- each pairwise stage launch, each GEMM launch of
+ * every 8th step, or (SDE_FLAG_FUSED) the run's GEMMs as one block (mean_ms
+ * per timed launch, total_ms summed over the timed events, launches = the
+ * launches they bracket).  Without that flag the
  * Kuramoto loop is bracketed as one launch.  Synchronises that stream.
  * sde_last_kernel_ms returns mean_ms.
  */

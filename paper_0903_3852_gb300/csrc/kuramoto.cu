@@ -1367,10 +1367,11 @@ cudaError_t ktime_begin(KuramotoCtx *k, cudaStream_t s) {
   return cudaEventRecord(k->kev[2 * k->kev_used], s);
 }
 
-cudaError_t ktime_end(KuramotoCtx *k, cudaStream_t s) {
+cudaError_t ktime_end(KuramotoCtx *k, cudaStream_t s, int64_t launches) {
   if (!(k->flags & SDE_FLAG_TIME_KERNELS)) return cudaSuccess;
   const cudaError_t err = cudaEventRecord(k->kev[2 * k->kev_used + 1], s);
   ++k->kev_used;
+  k->kev_launches += launches;
   return err;
 }
 
@@ -1384,8 +1385,9 @@ bool kuramoto_kernel_stats(KuramotoCtx *k, float *mean_ms, float *total_ms, int6
     tot += ms;
   }
   if (total_ms) *total_ms = (float)tot;
-  if (mean_ms) *mean_ms = (float)(tot / (double)k->kev_used);
-  if (launches) *launches = k->kev_used;
+  if (k->kev_launches == 0) return false;
+  if (mean_ms) *mean_ms = (float)(tot / (double)k->kev_launches);
+  if (launches) *launches = k->kev_launches;
   return true;
 }
 
@@ -1440,6 +1442,7 @@ sde_status kuramoto_run(KuramotoCtx *k, const sde_run_desc *r, cudaStream_t s, c
   SDE_CUDA_TRY(cudaGetLastError());
   const double inv2pi = 0.15915494309189533577;
   k->kev_used = 0;
+  k->kev_launches = 0;
   SDE_CUDA_TRY(cudaEventRecord(ev0, s));
   if (k->model == SDE_KURAMOTO_MEANFIELD && k->cs == 0) {
     sde_status st = run_meanfield_grid(k, r->n_begin, r->n_end, r->omega_dev, rbuf, n_rows, s);

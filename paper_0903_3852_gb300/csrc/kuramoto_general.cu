@@ -500,26 +500,26 @@ sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStrea
     return SDE_ERR_INVALID_ARG;
   }
   SDE_CUDA_TRY(launch_operand(k, 0, s));
+  // SDE_FLAG_TIME_KERNELS: an event between two GEMMs keeps the second one's
+  // prologue from overlapping the first one's end, so the fused form (back
+  // to back GEMMs, > 99 % of the loop) is timed as one block over all its
+  // launches (the r(t) samples in between included), and the separate form
+  // per GEMM launch on every kTimedStepStride-th step
+  const bool fused = is_tc(k) && (k->flags & SDE_FLAG_FUSED);
+  if (fused && r->n_end > r->n_begin) SDE_CUDA_TRY(ktime_begin(k, s));
   int64_t sample = 0;
   for (int64_t n = r->n_begin; n < r->n_end; ++n) {
     if (k->M > 0 && (n - r->n_begin) % k->M == 0) {
       SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
       ++sample;
     }
-    // GEMM launches are timed (SDE_FLAG_TIME_KERNELS) on every
-    // kTimedStepStride-th step only: an event between two GEMMs keeps the
-    // second one's prologue from overlapping the first one's end
-    const bool timed = (n - r->n_begin) % kTimedStepStride == 0;
-    if (is_tc(k) && (k->flags & SDE_FLAG_FUSED)) {
+    if (fused) {
       // the SRK2 sub-steps run in the GEMM epilogues
-      if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
       SDE_CUDA_TRY(launch_gemm(k, 0, s, tc::EPI_STAGE0, r->omega_dev, n, r->n_begin));
-      if (timed) SDE_CUDA_TRY(ktime_end(k, s));
-      if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
       SDE_CUDA_TRY(launch_gemm(k, 1, s, tc::EPI_STAGE1, r->omega_dev, n, r->n_begin));
-      if (timed) SDE_CUDA_TRY(ktime_end(k, s));
       continue;
     }
+    const bool timed = (n - r->n_begin) % kTimedStepStride == 0;
     if (timed) SDE_CUDA_TRY(ktime_begin(k, s));
     SDE_CUDA_TRY(launch_gemm(k, 0, s));
     if (timed) SDE_CUDA_TRY(ktime_end(k, s));
@@ -529,6 +529,7 @@ sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStrea
     if (timed) SDE_CUDA_TRY(ktime_end(k, s));
     SDE_CUDA_TRY(launch_stage<1>(k, 0, r->omega_dev, n, r->n_begin, s));
   }
+  if (fused && r->n_end > r->n_begin) SDE_CUDA_TRY(ktime_end(k, s, 2 * (r->n_end - r->n_begin)));
   if (k->M > 0) SDE_CUDA_TRY(kur_order_launch(k->theta, k->N, k->R, rbuf + sample * k->R, s));
   return SDE_OK;
 }

@@ -49,13 +49,14 @@ struct KuramotoCtx {
   void *gemm_plan = nullptr;
   // per-launch timing of the dominant kernel (SDE_FLAG_TIME_KERNELS)
   std::vector<cudaEvent_t> kev;
-  int64_t kev_used = 0;
+  int64_t kev_used = 0;      // event pairs recorded
+  int64_t kev_launches = 0;  // launches those pairs bracket
 };
 
 // Record the start / end of one launch of the dominant kernel when the
 // context times kernels; no-ops otherwise.
 cudaError_t ktime_begin(KuramotoCtx *k, cudaStream_t s);
-cudaError_t ktime_end(KuramotoCtx *k, cudaStream_t s);
+cudaError_t ktime_end(KuramotoCtx *k, cudaStream_t s, int64_t launches = 1);
 
 // Arguments of the mean-field kernel.
 struct KurArgs {
