@@ -535,6 +535,8 @@ def run_ours(args, rank, world, device):
         extra["fig4"] = {"r_end": float(obs["mean"][-1]), "r_theory": 0.8314620247541972,
                          "histogram_bins": nb, "counts": [int(c) for c in counts],
                          "paper_seconds_c1060_fp32": 20.0}
+    if args.workload == "kuramoto-general" and world == 1:
+        extra["library_gemm_same_shape"] = library_gemm_same_shape(N, R, device)
     k_ms = statistics.mean(kernel_ms)
     peaks, peak_src = measured_peaks()
     fp32 = measure_fp32_peak(device)
@@ -577,6 +579,11 @@ def run_ours(args, rank, world, device):
     elif args.workload == "kuramoto-fig4":
         traffic = 16.6 * w["n_osc"] * w["replicas"]  # mean over the launches of 4 steps
         traffic_src = "ncu capture of the grid-wide mean-field launches"
+    elif (args.workload == "kuramoto-general" and fused and not args.gemm_single_cta
+          and not args.gemm_stream_k):
+        traffic = 179.3e6  # K (134 MB) once, the operand and the SRK2 state of the epilogue
+        traffic_src = ("ncu capture of the fused CTA-pair GEMM (mean of its predictor and corrector "
+                       "launches)")
     elif args.workload == "kuramoto-meanfield":
         traffic = 2.43e6  # phases and omega read once per run; results stay in L2
         traffic_src = "ncu capture of the cluster mean-field kernel"
@@ -616,6 +623,33 @@ def run_ours(args, rank, world, device):
         res["plain_vs_batched"] = plain_comparison(args, device, res["value"], fp32["tflops"])
     res.update(extra)
     return res, ens
+
+
+def library_gemm_same_shape(N, R, device, reps=20):
+    """The same product as one general-coupling GEMM (N x N times N x 2R, BF16
+    operands) through torch.matmul (cuBLAS), timed with CUDA events after
+    warm-up: a library reference point for the tensor-core GEMM, outside the
+    timed region (median of `reps` launches; random operands)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(0)
+    A = torch.randn(N, N, device=device, dtype=torch.bfloat16, generator=g)
+    B = torch.randn(N, 2 * R, device=device, dtype=torch.bfloat16, generator=g)
+    for _ in range(5):
+        A @ B
+    ts = []
+    stream = torch.cuda.current_stream()
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        A @ B
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    t = statistics.median(ts)
+    del A, B
+    return {"shape": [N, 2 * R, N], "us": t * 1e3, "tflops": 2.0 * N * N * 2 * R / (t * 1e-3) / 1e12,
+            "how": "torch.matmul, BF16 operands and output (cuBLAS), median of %d launches, CUDA events" % reps}
 
 
 def plain_comparison(args, device, batched_rate, peak):
