@@ -215,6 +215,8 @@ struct GemmPlan {
   CUtensorMap mapOpHalf[2];  // box of 128 rows (one CTA's half of a pair tile)
   int bn = 0;
   bool pair = false;  // CTA-pair GEMM (tc_gemm2_bf16_kernel)
+  tc::EpiMaps em;     // pair GEMM: the SRK2 state its fused epilogue loads by TMA
+  float *omega_copy = nullptr;  // [R][N] the run's omega (a fixed address for em.omega)
   // stream-K GEMM (tc_gemm_sk_bf16_kernel): sk_P CTAs, 0 = whole tiles
   int sk_P = 0;
   float *ws = nullptr;        // [sk_P][256][128] partial sums
@@ -285,8 +287,8 @@ cudaError_t launch_tc2(KuramotoCtx *k, int which, const tc::StageArgs &sa, cudaS
   const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
   // clusters of two CTAs along x (the kernel's compile-time cluster shape)
   return launch_dependent(tc::tc_gemm2_bf16_kernel<EPI>, dim3(M / tc::BM, Ncols / tc::BN2),
-                          tc::EpiThreads<EPI>::value, tc::SMEM2_BYTES, s, g->mapK, g->mapOpHalf[which], k->P, M,
-                          Kdim, k->err, sa, k->wait_ns);
+                          tc::EpiThreads<EPI>::value, tc::SMEM2_BYTES, s, g->mapK, g->mapOpHalf[which], g->em, k->P,
+                          M, Kdim, k->err, sa, k->wait_ns);
 }
 
 template <int EPI>
@@ -395,6 +397,19 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
       st = make_map(&g->mapOpHalf[w], op_buf(k, w), 2 * k->R, k->N, tc::BH2);
       if (st != SDE_OK) return st;
     }
+    if (g->pair) {
+      if ((e = device_alloc((void **)&g->omega_copy, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+      const struct {
+        CUtensorMap *map;
+        const void *base;
+        int64_t planes;
+      } arrays[] = {{&g->em.theta, k->theta, 1},   {&g->em.theta_t, k->theta_t, 1}, {&g->em.g1, k->g1, 1},
+                    {&g->em.omega, g->omega_copy, 1}, {&g->em.psi, k->psi4, 4}};
+      for (const auto &a : arrays) {
+        st = make_map_w32(a.map, a.base, a.planes, k->R, k->N, tc::EQ_REPS, tc::BM);
+        if (st != SDE_OK) return st;
+      }
+    }
     const void *kernels[] = {
         (const void *)tc::tc_gemm_bf16_kernel<256, tc::EPI_STORE_D>,
         (const void *)tc::tc_gemm_bf16_kernel<256, tc::EPI_STAGE0>,
@@ -472,6 +487,7 @@ void kuramoto_general_free(KuramotoCtx *k) {
   if (k->gemm_plan) {
     cudaFree(((GemmPlan *)k->gemm_plan)->ws);
     cudaFree(((GemmPlan *)k->gemm_plan)->flags);
+    cudaFree(((GemmPlan *)k->gemm_plan)->omega_copy);
   }
   delete (GemmPlan *)k->gemm_plan;
   k->gemm_plan = nullptr;
@@ -506,6 +522,9 @@ sde_status kuramoto_general_run(KuramotoCtx *k, const sde_run_desc *r, cudaStrea
   // launches (the r(t) samples in between included), and the separate form
   // per GEMM launch on every kTimedStepStride-th step
   const bool fused = is_tc(k) && (k->flags & SDE_FLAG_FUSED);
+  if (fused && ((GemmPlan *)k->gemm_plan)->pair && r->n_end > r->n_begin)
+    SDE_CUDA_TRY(cudaMemcpyAsync(((GemmPlan *)k->gemm_plan)->omega_copy, r->omega_dev,
+                                 sizeof(float) * (size_t)k->N * (size_t)k->R, cudaMemcpyDeviceToDevice, s));
   if (fused && r->n_end > r->n_begin) SDE_CUDA_TRY(ktime_begin(k, s));
   int64_t sample = 0;
   for (int64_t n = r->n_begin; n < r->n_end; ++n) {

@@ -169,6 +169,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // An L2 policy that evicts first what it tags: for the coupling matrix, which
 // every GEMM streams once (read by the CTAs of one tile row at about the
 // same time), so that it does not push the SRK2 state the epilogues read out
@@ -290,6 +299,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Fused SRK2 sub-step of Eq. 2 in the epilogue (EPI_STAGE0 / EPI_STAGE1):
 // the tile's column pairs (2r, 2r+1) are P_s, P_c of replica r for the row's
 // oscillator i, so g = cos x_i P_s - sin x_i P_c is the coupling sum.
@@ -333,23 +355,50 @@ struct StageOut {
   float so, co;  // sin, cos of `out`: the next GEMM operand
 };
 
+// The phase update of one element given sin / cos of the phase the coupling
+// is taken at: g = cos x_i P_s - sin x_i P_c (its one rounding order fixed by
+// the explicit FMA), then theta~ (predictor) or the new theta (corrector).
+template <int STAGE>
+__device__ __forceinline__ uint32_t stage_phase(const StageArgs &a, uint32_t th, float omega, float psi, float g1,
+                                                float s, float c, float ps, float pc, float &g) {
+  g = fmaf(c, ps, -(s * pc));
+  const float wdt = omega * a.wscale;
+  if (STAGE == 0) {
+    const float d1 = fmaf(a.sc, psi, fmaf(a.kc, g, wdt));
+    return th + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
+  }
+  const float d = fmaf(a.sc, psi, fmaf(a.kh, g1 + g, wdt));
+  return th + (uint32_t)__float2int_rn(d * 4294967296.0f);
+}
+
 template <int STAGE>
 __device__ __forceinline__ StageOut stage_math(const StageArgs &a, uint32_t th_s, uint32_t th, float omega,
                                                float psi, float g1, float ps, float pc) {
   StageOut o;
   float s, c;
   sincos_turns(th_s, s, c);
-  o.g = c * ps - s * pc;
-  const float wdt = omega * a.wscale;
-  if (STAGE == 0) {
-    const float d1 = fmaf(a.sc, psi, fmaf(a.kc, o.g, wdt));
-    o.out = th + (uint32_t)__float2int_rn(d1 * 4294967296.0f);
-  } else {
-    const float d = fmaf(a.sc, psi, fmaf(a.kh, g1 + o.g, wdt));
-    o.out = th + (uint32_t)__float2int_rn(d * 4294967296.0f);
-  }
+  o.out = stage_phase<STAGE>(a, th, omega, psi, g1, s, c, ps, pc, o.g);
   sincos_turns(o.out, o.so, o.co);
   return o;
+}
+
+// The same for two elements at once, the sin/cos polynomials on packed FP32
+// pairs (sincos_turns2: the same roundings as sincos_turns per element), so
+// the results equal stage_math's bit for bit.
+template <int STAGE>
+__device__ __forceinline__ void stage_math2(const StageArgs &a, const uint32_t (&th_s)[2], const uint32_t (&th)[2],
+                                            const float (&omega)[2], const float (&psi)[2], const float (&g1)[2],
+                                            const float (&ps)[2], const float (&pc)[2], StageOut (&o)[2]) {
+  float2 s, c;
+  sincos_turns2(th_s[0], th_s[1], s, c);
+  o[0].out = stage_phase<STAGE>(a, th[0], omega[0], psi[0], g1[0], s.x, c.x, ps[0], pc[0], o[0].g);
+  o[1].out = stage_phase<STAGE>(a, th[1], omega[1], psi[1], g1[1], s.y, c.y, ps[1], pc[1], o[1].g);
+  float2 so, co;
+  sincos_turns2(o[0].out, o[1].out, so, co);
+  o[0].so = so.x;
+  o[0].co = co.x;
+  o[1].so = so.y;
+  o[1].co = co.y;
 }
 
 // The Gaussian of step n for element idx: drawn from the Philox block at the
@@ -397,12 +446,19 @@ __device__ __forceinline__ void stage_group(const StageArgs &a, int64_t r0, int6
     g1[j] = STAGE == 1 ? a.g1[idx] : 0.0f;
     psi[j] = (STAGE == 0 && a.fresh) ? 0.0f : a.psi4[(a.n & 3) * a.NR + idx];
   }
+  static_assert(NB % 2 == 0, "replicas in pairs");
 #pragma unroll
-  for (int j = 0; j < NB; ++j) {
+  for (int j = 0; j < NB; j += 2) {
     const int64_t r = r0 + j, idx = r * a.N + i;
-    if (STAGE == 0 && a.fresh) psi[j] = stage_noise<STAGE>(a, r, i, idx, key);
-    const StageOut o = stage_math<STAGE>(a, th_s[j], th[j], om[j], psi[j], g1[j], v[2 * j], v[2 * j + 1]);
-    stage_store<STAGE>(a, a.op_next, r, i, idx, o);
+    if (STAGE == 0 && a.fresh) {
+      psi[j] = stage_noise<STAGE>(a, r, i, idx, key);
+      psi[j + 1] = stage_noise<STAGE>(a, r + 1, i, idx + a.N, key);
+    }
+    StageOut o[2];
+    stage_math2<STAGE>(a, {th_s[j], th_s[j + 1]}, {th[j], th[j + 1]}, {om[j], om[j + 1]}, {psi[j], psi[j + 1]},
+                       {g1[j], g1[j + 1]}, {v[2 * j], v[2 * j + 2]}, {v[2 * j + 1], v[2 * j + 3]}, o);
+    stage_store<STAGE>(a, a.op_next, r, i, idx, o[0]);
+    stage_store<STAGE>(a, a.op_next, r + 1, i, idx + a.N, o[1]);
   }
 }
 
@@ -579,6 +635,98 @@ constexpr int STAGE2_BYTES = A2_BYTES + B2_BYTES;  // one CTA's half of a slot
 constexpr int SMEM2_BYTES = STAGES2 * STAGE2_BYTES + 1024;
 constexpr int TMEM2_COLS = BN2;
 
+// The SRK2 state an epilogue reads, as TMA tensor maps of 4-byte words over
+// [R][N] (psi: the four planes [4][R][N]), boxes of 128 oscillators x 32
+// replicas.
+struct EpiMaps {
+  CUtensorMap theta, theta_t, g1, omega, psi;
+};
+
+constexpr int EQ_REPS = 32;                     // replicas per quarter of a tile
+constexpr int EQ_ARR_BYTES = EQ_REPS * BM * 4;  // one array's box: 16 KB
+constexpr int EQ_BUF_BYTES = 5 * EQ_ARR_BYTES;  // theta, omega, psi, theta~, g1
+static_assert(2 * EQ_BUF_BYTES <= STAGES2 * STAGE2_BYTES, "epilogue inputs must fit in the ring");
+
+// The fused SRK2 sub-step of the CTA-pair GEMM, after its MMAs: the inputs
+// of the CTA's 128 oscillators x 128 replicas (theta, omega, the Gaussians
+// and, for the corrector, theta~ and the first-stage sums) come into the now
+// idle ring by TMA, a quarter of the replicas (32) at a time in two
+// alternating buffers, so that one quarter loads while the previous one is
+// finished.  Warp w: TMEM lane quarter w % 4 (its 32 oscillators), replicas
+// 8 (w / 4) .. 8 (w / 4) + 7 of each quarter.  Thread 0 issues the loads; the
+// buffer of quarter c is reloaded for quarter c + 2 once every warp has
+// released it.  Same arithmetic as stage_group on the same values.
+template <int EPI>
+__device__ __forceinline__ void pair_stage_epilogue(uint32_t tmem, int m0, int n0, const StageArgs &sa,
+                                                    const EpiMaps &em, uint8_t *smem, uint64_t *epi_full,
+                                                    uint64_t *epi_free) {
+  constexpr int STAGE = EPI == EPI_STAGE1 ? 1 : 0;
+  constexpr int W = EQ_ARR_BYTES / 4;  // words per array box
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lq = warp & 3, grp = warp >> 2;
+  const int row_l = lq * 32 + lane;
+  const int64_t i = m0 + row_l;
+  const int na = STAGE == 1 ? 5 : (sa.fresh ? 2 : 3);
+  const uint2 key = seed_to_key(sa.seed);
+  volatile int no_abort = 0;
+  auto issue = [&](int c) {
+    uint8_t *buf = smem + (c & 1) * EQ_BUF_BYTES;
+    uint64_t *bar = &epi_full[c & 1];
+    const int r0 = n0 / 2 + EQ_REPS * c;
+    mbar_arrive_expect_tx(bar, (uint32_t)(na * EQ_ARR_BYTES));
+    tma_load_2d(buf, &em.theta, bar, m0, r0);
+    tma_load_2d(buf + EQ_ARR_BYTES, &em.omega, bar, m0, r0);
+    if (na >= 3) tma_load_3d(buf + 2 * EQ_ARR_BYTES, &em.psi, bar, m0, r0, (int)(sa.n & 3));
+    if (STAGE == 1) {
+      tma_load_2d(buf + 3 * EQ_ARR_BYTES, &em.theta_t, bar, m0, r0);
+      tma_load_2d(buf + 4 * EQ_ARR_BYTES, &em.g1, bar, m0, r0);
+    }
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    issue(1);
+  }
+#pragma unroll 1
+  for (int c = 0; c < BN2 / 2 / EQ_REPS; ++c) {
+    mbar_wait(&epi_full[c & 1], (uint32_t)(c >> 1) & 1u, &no_abort);
+    __syncwarp();
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(2 * EQ_REPS * c + 16 * grp), v);
+    const uint32_t *buf = (const uint32_t *)(smem + (c & 1) * EQ_BUF_BYTES);
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      uint32_t th[2], th_s[2];
+      float om[2], psi[2], g1[2];
+      int64_t r[2], idx[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rl = 8 * grp + j + h;  // replica within the quarter
+        r[h] = n0 / 2 + EQ_REPS * c + rl;
+        idx[h] = r[h] * sa.N + i;
+        const int o = rl * BM + row_l;
+        th[h] = buf[o];
+        om[h] = __uint_as_float(buf[W + o]);
+        psi[h] = (STAGE == 0 && sa.fresh) ? stage_noise<0>(sa, r[h], i, idx[h], key) : __uint_as_float(buf[2 * W + o]);
+        th_s[h] = STAGE == 0 ? th[h] : buf[3 * W + o];
+        g1[h] = STAGE == 1 ? __uint_as_float(buf[4 * W + o]) : 0.0f;
+      }
+      StageOut out[2];
+      stage_math2<STAGE>(sa, th_s, th, om, psi, g1, {v[2 * j], v[2 * j + 2]}, {v[2 * j + 1], v[2 * j + 3]}, out);
+      stage_store<STAGE>(sa, sa.op_next, r[0], i, idx[0], out[0]);
+      stage_store<STAGE>(sa, sa.op_next, r[1], i, idx[1], out[1]);
+    }
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&epi_free[c & 1])) : "memory");
+    if (threadIdx.x == 0 && c + 2 < BN2 / 2 / EQ_REPS) {
+      mbar_wait(&epi_free[c & 1], (uint32_t)(c >> 1) & 1u, &no_abort);
+      // the buffer's last readers were generic loads; order them before the
+      // TMA's writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(c + 2);
+    }
+  }
+}
+
 // D = A * B^T, tile rows m0 = 128 * blockIdx.x (the pair covers 256 rows),
 // columns n0 = 256 * blockIdx.y.  mapB's box is 128 rows (half a tile).
 // Requires M % 256 == 0, Ncols % 256 == 0, Kdim % 64 == 0 (checked by the
@@ -586,8 +734,8 @@ constexpr int TMEM2_COLS = BN2;
 template <int EPI>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::value, 1)
     tc_gemm2_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                         float *__restrict__ Dt, int M, int Kdim, uint32_t *err, const StageArgs sa,
-                         uint64_t wait_ns) {
+                         const __grid_constant__ EpiMaps em, float *__restrict__ Dt, int M, int Kdim, uint32_t *err,
+                         const StageArgs sa, uint64_t wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *smA = smem;
@@ -599,6 +747,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
   __shared__ int abort_flag;
   __shared__ int issued_cnt;    // K slices whose loads this CTA issued
   __shared__ int consumed_cnt;  // even CTA: K slices whose MMAs were issued
+  __shared__ __align__(8) uint64_t epi_full[2];  // SRK2 epilogue: a quarter's inputs landed
+  __shared__ __align__(8) uint64_t epi_free[2];  // SRK2 epilogue: every warp is done with a buffer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_ctarank();
@@ -611,6 +761,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&epi_full[b], 1);
+      mbar_init(&epi_free[b], EpiThreads<EPI>::value / 32);
+    }
     abort_flag = 0;
     issued_cnt = 0;
     consumed_cnt = 0;
@@ -630,17 +784,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
   cluster_barrier();  // both CTAs' barriers initialised, tensor memory allocated
   tmem_fence_after();
   const uint32_t tmem = tmem_slot;
+  // The coupling matrix (A) is written only before a run, so the first slots'
+  // A loads may start while the previous kernel of the stream finishes; the
+  // operand (B) and the SRK2 state are read only after griddepcontrol.wait.
+  const int pre = nk < STAGES2 ? nk : STAGES2;
+  const int b_row = n0 + (int)rank * BH2;
+  uint64_t pol_a = 0;
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
+    pol_a = l2_evict_first_policy();
+    for (int kb = 0; kb < pre; ++kb) {  // fresh slots: nothing to wait for
+      if (rank == 0) mbar_arrive_expect_tx(&full_bar[kb], 2u * (uint32_t)STAGE2_BYTES);
+      tma_load_2d_pair_hint(smA + kb * A2_BYTES, &mapA, mapa_shared(&full_bar[kb], 0), kb * BK, m0, pol_a);
+    }
+  }
   griddep_wait();  // as in the one-CTA kernel
   griddep_launch_dependents();
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer (both CTAs, each its own half) ----
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&mapB) : "memory");
-    const int b_row = n0 + (int)rank * BH2;
-    const uint64_t pol_a = l2_evict_first_policy();
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
+    for (int kb = 0; kb < pre; ++kb)
+      tma_load_2d_pair(smB + kb * B2_BYTES, &mapB, mapa_shared(&full_bar[kb], 0), kb * BK, b_row);
+    int issued = pre;
+    for (int kb = pre; kb < nk; ++kb) {
       const int s = kb % STAGES2;
       const uint32_t ph = (uint32_t)(kb / STAGES2) & 1u;
       if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag, wait_ns)) break;
@@ -694,7 +861,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
   }
   // ---- epilogue: all warps of both CTAs, each CTA its own 128 rows ----
   tmem_fence_after();
-  if (ok) epilogue_tile<BN2, EPI>(tmem, m0, n0, Dt, M, sa);
+  if (ok) {
+    if (EPI == EPI_STORE_D)
+      epilogue_tile<BN2, EPI>(tmem, m0, n0, Dt, M, sa);
+    else
+      pair_stage_epilogue<EPI>(tmem, m0, n0, sa, em, smem, epi_full, epi_free);
+  }
   tmem_fence_before();
   // neither CTA frees the pair's tensor memory or leaves (with its barriers
   // and shared memory) while the other, or a load, may still use them
