@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) kg_stage_kernel(const float *__restrict__
     th_s[u] = STAGE == 0 ? th[u] : a.theta_t[idx];
     om[u] = a.omega[idx];
     g1[u] = STAGE == 1 ? a.g1[idx] : 0.0f;
-    psi[u] = (STAGE == 0 && a.fresh) ? 0.0f : a.psi4[(a.n & 3) * a.NR + idx];
+    psi[u] = (STAGE == 0 && a.fresh) ? 0.0f : tc::psi_plane(a, a.n >> 2, (int)(a.n & 3))[idx];
   }
 #pragma unroll
   for (int u = 0; u < kStageIlp; ++u) {
@@ -244,6 +244,7 @@ tc::StageArgs stage_args(KuramotoCtx *k, int next, const float *omega, int64_t n
   a.NR = k->N * k->R;
   a.n = n;
   a.fresh = ((n & 3) == 0 || n == run_begin) ? 1 : 0;
+  a.pre_slice = -1;
   a.wscale = (float)(k->dt * inv2pi);
   a.kc = (float)(k->dt * inv2pi);
   a.kh = (float)(0.5 * k->dt * inv2pi);
@@ -310,7 +311,15 @@ cudaError_t launch_gemm(KuramotoCtx *k, int which, cudaStream_t s, int epi = tc:
   const int M = (int)k->N, Ncols = (int)(2 * k->R), Kdim = (int)k->N;
   if (is_tc(k)) {
     GemmPlan *g = (GemmPlan *)k->gemm_plan;
-    const tc::StageArgs sa = stage_args(k, epi == tc::EPI_STORE_D ? -1 : 1 - which, omega, n, run_begin);
+    tc::StageArgs sa = stage_args(k, epi == tc::EPI_STORE_D ? -1 : 1 - which, omega, n, run_begin);
+    if (g->pair && g->sk_P == 0 && epi != tc::EPI_STORE_D) {
+      // the fused CTA-pair GEMMs of a Philox block draw the next block ahead,
+      // a slice per launch; a block whose predecessor lay wholly in this run
+      // is not drawn again at its first step
+      const int64_t block = n >> 2;
+      if (4 * block >= run_begin) sa.pre_slice = (int32_t)(2 * (n & 3) + (epi == tc::EPI_STAGE1 ? 1 : 0));
+      if (block >= 1 && 4 * (block - 1) >= run_begin && n != run_begin) sa.fresh = 0;
+    }
     if (g->sk_P > 0) {
       if (epi == tc::EPI_STAGE0) return launch_sk<tc::EPI_STAGE0>(k, which, sa, s);
       if (epi == tc::EPI_STAGE1) return launch_sk<tc::EPI_STAGE1>(k, which, sa, s);
@@ -381,7 +390,7 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
   if ((e = device_alloc((void **)&k->theta_t, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = device_alloc((void **)&k->g1, NR * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if ((e = device_alloc((void **)&k->P, NR * 2 * 4)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-  if ((e = device_alloc((void **)&k->psi4, NR * 4 * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  if ((e = device_alloc((void **)&k->psi4, NR * 8 * sizeof(float))) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
   if (is_tc(k)) {
     if ((e = device_alloc((void **)&k->Kbf16, NN * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     if ((e = device_alloc((void **)&k->Bt, NR * 2 * 2 * 2)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
@@ -404,7 +413,7 @@ sde_status kuramoto_general_alloc(KuramotoCtx *k) {
         const void *base;
         int64_t planes;
       } arrays[] = {{&g->em.theta, k->theta, 1},   {&g->em.theta_t, k->theta_t, 1}, {&g->em.g1, k->g1, 1},
-                    {&g->em.omega, g->omega_copy, 1}, {&g->em.psi, k->psi4, 4}};
+                    {&g->em.omega, g->omega_copy, 1}, {&g->em.psi, k->psi4, 8}};
       for (const auto &a : arrays) {
         st = make_map_w32(a.map, a.base, a.planes, k->R, k->N, tc::EQ_REPS, tc::BM);
         if (st != SDE_OK) return st;

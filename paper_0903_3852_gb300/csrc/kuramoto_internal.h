@@ -44,7 +44,7 @@ struct KuramotoCtx {
   __nv_bfloat16 *Bt = nullptr;    // [2R][N] sin / cos rows (BF16 operand)
   float *Bt32 = nullptr;          // [2R][N] sin / cos rows (FP32 operand)
   float *P = nullptr;             // [2R][N] GEMM output (transposed)
-  float *psi4 = nullptr;          // [4][R][N] Gaussians of the current 4-step Philox block
+  float *psi4 = nullptr;          // general: [2][4][R][N] Gaussians of two 4-step Philox blocks; grid-wide mean field: [3][R][N]
   bool have_K = false;
   void *gemm_plan = nullptr;
   // per-launch timing of the dominant kernel (SDE_FLAG_TIME_KERNELS)

@@ -319,18 +319,25 @@ struct StageArgs {
   uint32_t *theta;     // [R][N] fixed-point turns
   uint32_t *theta_t;   // [R][N] predictor phases
   float *g1;           // [R][N] first-stage coupling sums
-  float *psi4;         // [4][R][N] Gaussians of the current 4-step Philox block, one plane per step
+  float *psi4;         // [2][4][R][N] Gaussians of 4-step Philox blocks, one plane per step; block g in half g % 2
   const float *omega;  // [R][N]
   __nv_bfloat16 *op_next;  // [2R][N] operand of the next GEMM (the buffer this GEMM does not read)
   int64_t N;
   int64_t NR;     // N * R: plane stride of psi4
   int64_t n;      // step index
-  int32_t fresh;  // stage 0: draw the Philox block of step n (n % 4 == 0 or first step of a run)
+  int32_t fresh;  // stage 0: draw the Philox block of step n (its first step or the run's, unless drawn ahead)
+  int32_t pre_slice;  // CTA-pair GEMM with the fused sub-step: draw slice pre_slice (0..7) of the next block
+                      // while the MMAs run (the block's eight launches draw all of it); -1: none
   float wscale, kc, kh, sc;
   uint64_t seed;
 };
 
 enum { EPI_STORE_D = 0, EPI_STAGE0 = 1, EPI_STAGE1 = 2 };
+
+// Plane q (the block's step q) of the Gaussians of Philox block `block`.
+__device__ __forceinline__ float *psi_plane(const StageArgs &a, int64_t block, int q) {
+  return a.psi4 + ((block & 1) * 4 + q) * a.NR;
+}
 
 
 // One element of a stage: oscillator i of replica r with coupling
@@ -410,10 +417,10 @@ __device__ __forceinline__ float stage_noise(const StageArgs &a, int64_t r, int6
   if (STAGE == 0 && a.fresh) {
     float zz[4];
     gauss4((uint32_t)(a.n >> 2), (uint32_t)i, (uint32_t)r, kTagKuramoto, key, zz);
-    for (int k = q; k < 4; ++k) a.psi4[k * a.NR + idx] = zz[k];
+    for (int k = q; k < 4; ++k) psi_plane(a, a.n >> 2, k)[idx] = zz[k];
     return pick4(zz, q);
   }
-  return a.psi4[q * a.NR + idx];
+  return psi_plane(a, a.n >> 2, q)[idx];
 }
 
 template <int STAGE, typename T>
@@ -444,7 +451,7 @@ __device__ __forceinline__ void stage_group(const StageArgs &a, int64_t r0, int6
     th_s[j] = STAGE == 0 ? th[j] : a.theta_t[idx];
     om[j] = a.omega[idx];
     g1[j] = STAGE == 1 ? a.g1[idx] : 0.0f;
-    psi[j] = (STAGE == 0 && a.fresh) ? 0.0f : a.psi4[(a.n & 3) * a.NR + idx];
+    psi[j] = (STAGE == 0 && a.fresh) ? 0.0f : psi_plane(a, a.n >> 2, (int)(a.n & 3))[idx];
   }
   static_assert(NB % 2 == 0, "replicas in pairs");
 #pragma unroll
@@ -636,7 +643,7 @@ constexpr int SMEM2_BYTES = STAGES2 * STAGE2_BYTES + 1024;
 constexpr int TMEM2_COLS = BN2;
 
 // The SRK2 state an epilogue reads, as TMA tensor maps of 4-byte words over
-// [R][N] (psi: the four planes [4][R][N]), boxes of 128 oscillators x 32
+// [R][N] (psi: the eight planes [2][4][R][N]), boxes of 128 oscillators x 32
 // replicas.
 struct EpiMaps {
   CUtensorMap theta, theta_t, g1, omega, psi;
@@ -676,7 +683,8 @@ __device__ __forceinline__ void pair_stage_epilogue(uint32_t tmem, int m0, int n
     mbar_arrive_expect_tx(bar, (uint32_t)(na * EQ_ARR_BYTES));
     tma_load_2d(buf, &em.theta, bar, m0, r0);
     tma_load_2d(buf + EQ_ARR_BYTES, &em.omega, bar, m0, r0);
-    if (na >= 3) tma_load_3d(buf + 2 * EQ_ARR_BYTES, &em.psi, bar, m0, r0, (int)(sa.n & 3));
+    if (na >= 3)
+      tma_load_3d(buf + 2 * EQ_ARR_BYTES, &em.psi, bar, m0, r0, (int)(((sa.n >> 2) & 1) * 4 + (sa.n & 3)));
     if (STAGE == 1) {
       tma_load_2d(buf + 3 * EQ_ARR_BYTES, &em.theta_t, bar, m0, r0);
       tma_load_2d(buf + 4 * EQ_ARR_BYTES, &em.g1, bar, m0, r0);
@@ -801,6 +809,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
   }
   griddep_wait();  // as in the one-CTA kernel
   griddep_launch_dependents();
+
+  if (EPI != EPI_STORE_D && sa.pre_slice >= 0 && warp >= 2) {
+    // The warps that wait for the accumulators draw a slice of the next
+    // Philox block of this CTA's elements meanwhile: replicas 16 pre_slice ..
+    // 16 pre_slice + 15 of the tile, all 128 oscillators, four Gaussians
+    // each, into the other half of psi4 (its last readers were the previous
+    // block's launches, which are complete).
+    const uint32_t gnext = (uint32_t)(sa.n >> 2) + 1u;
+    const uint2 key = seed_to_key(sa.seed);
+#pragma unroll 1
+    for (int e = (int)threadIdx.x - 64; e < 16 * BM; e += EpiThreads<EPI>::value - 64) {
+      const int64_t r = n0 / 2 + 16 * sa.pre_slice + (e >> 7), i = m0 + (e & (BM - 1));
+      const int64_t idx = r * sa.N + i;
+      float zz[4];
+      gauss4(gnext, (uint32_t)i, (uint32_t)r, kTagKuramoto, key, zz);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) psi_plane(sa, gnext, k)[idx] = zz[k];
+    }
+  }
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer (both CTAs, each its own half) ----

@@ -145,10 +145,15 @@ def test_size_validation():
         ens.run_kuramoto(0, 1, phi, torch.empty_like(phi), phi)
 
 
-@pytest.mark.parametrize("N,R,gemm", [(1024, 128, 0), (2048, 128, sde.SDE_FLAG_GEMM_STREAM_K)])
-def test_fused_epilogue_equals_separate_stage_kernels(N, R, gemm):
+# whole pair tiles from step 0 and from step 13 (inside a Philox block: the
+# fused pair GEMMs draw each next block ahead only once a whole block of the
+# run lies behind it), and the stream-K GEMM
+@pytest.mark.parametrize("N,R,gemm,n0", [(1024, 128, 0, 0), (1024, 128, 0, 13),
+                                         (2048, 128, sde.SDE_FLAG_GEMM_STREAM_K, 0)])
+def test_fused_epilogue_equals_separate_stage_kernels(N, R, gemm, n0):
     # the SRK2 sub-step in the GEMM epilogue computes the same expression on
-    # the same FP32 accumulators as the separate stage kernels: bit-identical
+    # the same FP32 accumulators, with the same Gaussians, as the separate
+    # stage kernels: bit-identical
     steps = 37
     w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=12)
     outs = []
@@ -158,7 +163,7 @@ def test_fused_epilogue_equals_separate_stage_kernels(N, R, gemm):
                                     flags=flags | gemm)
         assert ens.tuning()[2] == (0 if gemm else 2)
         ens.set_coupling(torch.from_numpy(w["Kmat"]).cuda())
-        outs.append(kur_run(ens, w["phi0"], w["omega"], 0, steps))
+        outs.append(kur_run(ens, w["phi0"], w["omega"], n0, n0 + steps))
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
 
