@@ -581,7 +581,7 @@ def run_ours(args, rank, world, device):
         traffic_src = "ncu capture of the grid-wide mean-field launches"
     elif (args.workload == "kuramoto-general" and fused and not args.gemm_single_cta
           and not args.gemm_stream_k):
-        traffic = 179.3e6  # K (134 MB) once, the operand and the SRK2 state of the epilogue
+        traffic = 179.4e6  # K (134 MB) once, the operand and the SRK2 state of the epilogue
         traffic_src = ("ncu capture of the fused CTA-pair GEMM (mean of its predictor and corrector "
                        "launches)")
     elif args.workload == "kuramoto-meanfield":
