@@ -22,6 +22,13 @@
 // the argument: the producer always waits for its last loads to land, and
 // every thread waits for the commit that follows the last MMA, before the
 // tensor memory is freed and the CTA returns.
+//
+// Two kernels: tc_gemm_bf16_kernel (one CTA per 128 x BN tile, described
+// above) and tc_gemm2_bf16_kernel (one 256 x 256 tile per cluster of two
+// CTAs, tcgen05 cta_group::2; its own notes below), the default where the
+// sizes allow.  Both launch with programmatic dependent launch: their set-up
+// runs before griddepcontrol.wait, everything the previous kernel wrote is
+// read after it.  tc_gemm_sk.cuh holds the stream-K form.
 #pragma once
 
 #include <cuda.h>
