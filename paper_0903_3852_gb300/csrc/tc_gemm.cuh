@@ -670,10 +670,12 @@ static_assert(2 * EQ_BUF_BYTES <= STAGES2 * STAGE2_BYTES, "epilogue inputs must 
 // 8 (w / 4) .. 8 (w / 4) + 7 of each quarter.  Thread 0 issues the loads; the
 // buffer of quarter c is reloaded for quarter c + 2 once every warp has
 // released it.  Same arithmetic as stage_group on the same values.
+// A wait that expires (the fixed one-second bound) records kErrTimeout in
+// *err: the quarter's results are then not to be trusted.
 template <int EPI>
 __device__ __forceinline__ void pair_stage_epilogue(uint32_t tmem, int m0, int n0, const StageArgs &sa,
                                                     const EpiMaps &em, uint8_t *smem, uint64_t *epi_full,
-                                                    uint64_t *epi_free) {
+                                                    uint64_t *epi_free, uint32_t *err) {
   constexpr int STAGE = EPI == EPI_STAGE1 ? 1 : 0;
   constexpr int W = EQ_ARR_BYTES / 4;  // words per array box
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -703,7 +705,7 @@ __device__ __forceinline__ void pair_stage_epilogue(uint32_t tmem, int m0, int n
   }
 #pragma unroll 1
   for (int c = 0; c < BN2 / 2 / EQ_REPS; ++c) {
-    mbar_wait(&epi_full[c & 1], (uint32_t)(c >> 1) & 1u, &no_abort);
+    if (!mbar_wait(&epi_full[c & 1], (uint32_t)(c >> 1) & 1u, &no_abort)) atomicOr(err, kErrTimeout);
     __syncwarp();
     float v[16];
     tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(2 * EQ_REPS * c + 16 * grp), v);
@@ -733,7 +735,7 @@ __device__ __forceinline__ void pair_stage_epilogue(uint32_t tmem, int m0, int n
     __syncwarp();
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&epi_free[c & 1])) : "memory");
     if (threadIdx.x == 0 && c + 2 < BN2 / 2 / EQ_REPS) {
-      mbar_wait(&epi_free[c & 1], (uint32_t)(c >> 1) & 1u, &no_abort);
+      if (!mbar_wait(&epi_free[c & 1], (uint32_t)(c >> 1) & 1u, &no_abort)) atomicOr(err, kErrTimeout);
       // the buffer's last readers were generic loads; order them before the
       // TMA's writes
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -899,7 +901,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(EpiThreads<EPI>::val
     if (EPI == EPI_STORE_D)
       epilogue_tile<BN2, EPI>(tmem, m0, n0, Dt, M, sa);
     else
-      pair_stage_epilogue<EPI>(tmem, m0, n0, sa, em, smem, epi_full, epi_free);
+      pair_stage_epilogue<EPI>(tmem, m0, n0, sa, em, smem, epi_full, epi_free, err);
   }
   tmem_fence_before();
   // neither CTA frees the pair's tensor memory or leaves (with its barriers
