@@ -221,3 +221,23 @@ def test_injected_allocation_failure_reports_no_memory(L):
     if st == sde.SDE_OK:
         L.sde_destroy(h)
     assert L.sde_set_wait_limit(None, 5) == sde.SDE_ERR_INVALID_ARG
+
+
+def test_binding_constants_equal_the_header(tmp_path):
+    # every status, model, schedule and flag the binding names, printed by a C
+    # program compiled against include/sde.h
+    names = [n for n in dir(sde) if n.startswith("SDE_") and isinstance(getattr(sde, n), int)]
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "sde.h"\nint main(void) {\n'
+                   + "".join('  printf("%s %%lld\\n", (long long)(%s));\n' % (n, n) for n in names)
+                   + '  printf("SDE_NOALLOC_MAX_PATHS %lld\\n", (long long)SDE_NOALLOC_MAX_PATHS);\n'
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).split("\n") if l)
+    assert len(names) >= 20
+    for n in names:
+        assert int(got[n]) == getattr(sde, n), n
+    assert int(got["SDE_NOALLOC_MAX_PATHS"]) == sde.NOALLOC_MAX_PATHS
+    flags = [getattr(sde, n) for n in names if n.startswith("SDE_FLAG_")]
+    assert all(f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)  # distinct single bits
