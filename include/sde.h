@@ -515,7 +515,9 @@ sde_status sde_mlp_train_step_members(sde_mlp *mlp, const float *X_dev, const fl
 sde_status sde_fp32_fma_probe(int32_t packed, int64_t iters, int32_t grid, int32_t block, float *sink_dev,
                               double *flop_host, void *stream);
 
-/* Version of this ABI (major * 100 + minor). */
+/* Version of this ABI (major * 100 + minor).  102: the general-coupling GEMM
+   forms (SDE_FLAG_GEMM_SINGLE_CTA, SDE_FLAG_GEMM_STREAM_K) and their
+   sde_get_tuning values. */
 int32_t sde_abi_version(void);
 
 #ifdef __cplusplus

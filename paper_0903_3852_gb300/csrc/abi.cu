@@ -440,7 +440,7 @@ sde_status run_graph(sde_ctx *c, const sde_run_desc *r, cudaStream_t s) {
 
 extern "C" {
 
-int32_t sde_abi_version(void) { return 101; }
+int32_t sde_abi_version(void) { return 102; }
 
 const char *sde_last_error(void) { return g_last_error.c_str(); }
 

@@ -75,7 +75,7 @@ int main(void) {
 
 
 def test_validation_before_any_cuda_call(L):
-    assert L.sde_abi_version() == 101
+    assert L.sde_abi_version() == 102
     h = ctypes.c_void_p()
     assert L.sde_create(None, ctypes.byref(h)) == 1
     assert b"cfg" in L.sde_last_error()
