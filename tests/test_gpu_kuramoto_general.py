@@ -84,11 +84,17 @@ def test_fp32_general_pathwise():
         assert np.max(np.abs(rg[:, r] - ro)) <= 2e-5
 
 
-def test_bf16_general_r_of_t_on_512_slice_within_3se():
-    N, R, steps, M = 512, 64, 200, 50
-    Ro = 8  # replicas the O(N^2)-per-stage oracle integrates (the GPU runs all 64)
+# 64 replicas: the one-CTA GEMM and separate stage kernels; 128 replicas: the
+# CTA-pair GEMM with the SRK2 sub-step fused into its epilogue (the bench's
+# form: staged inputs, the Philox blocks drawn ahead)
+@pytest.mark.parametrize("R,flags,cluster", [(64, 0, 1), (128, sde.SDE_FLAG_FUSED, 2)])
+def test_bf16_general_r_of_t_on_512_slice_within_3se(R, flags, cluster):
+    N, steps, M = 512, 200, 50
+    Ro = 8  # replicas the O(N^2)-per-stage oracle integrates (the GPU runs all R)
     w = inputs.kuramoto_general(n_osc=N, replicas=R, seed=4)
-    ens = _ens(sde.SDE_KURAMOTO_GENERAL, N, R, 0.02, 0.005, 5, M=M)
+    ensure_built()
+    ens = sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, 0.02, 0.005, 5, sample_every=M, flags=flags)
+    assert ens.tuning()[2] == cluster
     ens.set_coupling(torch.from_numpy(w["Kmat"]).cuda())
     phig, rg_all, obs = kur_run(ens, w["phi0"], w["omega"], 0, steps)
     K = w["Kmat"].astype(np.float64)
