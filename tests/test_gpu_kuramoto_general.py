@@ -134,9 +134,20 @@ def test_full_size_sampled_rows():
     absK = np.abs(w["Kmat"][rows].astype(np.float64)).sum(axis=1)[None, :]
     print("full size: max err %.3e rms %.3e" % (err.max(), math.sqrt(np.mean(err ** 2))))
     assert np.all(err <= 2.0 ** -7 * absK)
-    # a short run at full size stays finite and produces r(t) rows
-    phig, rg, obs = kur_run(ens, w["phi0"], w["omega"], 0, 20)
-    assert np.all(np.isfinite(phig)) and obs.shape[0] == 2
+    # a short run at full size stays finite and produces r(t) rows; the bench's
+    # form (the SRK2 sub-step fused into the CTA-pair GEMM, Philox blocks drawn
+    # ahead) gives the same phases and r(t) bit for bit, from step 0 and from
+    # a step inside a Philox block
+    for n0 in (0, 6):
+        phig, rg, obs = kur_run(ens, w["phi0"], w["omega"], n0, n0 + 20)
+        assert np.all(np.isfinite(phig)) and obs.shape[0] == 2
+        fused = sde.Ensemble.kuramoto(sde.SDE_KURAMOTO_GENERAL, N, R, 0.0, w["D"], w["dt"], w["seed"],
+                                      sample_every=100, flags=sde.SDE_FLAG_FUSED)
+        assert fused.tuning()[2] == 2
+        fused.set_coupling(torch.from_numpy(w["Kmat"]).cuda())
+        phif, rf, _ = kur_run(fused, w["phi0"], w["omega"], n0, n0 + 20)
+        assert np.array_equal(phif, phig) and np.array_equal(rf, rg)
+        fused.close()
 
 
 def test_size_validation():
